@@ -1,0 +1,179 @@
+"""Seeded synthetic workloads for the k-NN / eps-NN time-warping scan.
+
+This module only draws random numbers and lays them out; it holds none of the
+method's arithmetic (no distance, bound or envelope).  Both the FP64 oracle's
+tests and the GPU path consume what it returns.
+
+Recipe (class-structured warped random walks, standing in for the RAM/CBF
+generators and the real data sets of Section 5, which are not available):
+
+* class template: a random walk ``cumsum(N(0,1))`` per dimension;
+  for correlated channels (motion-capture-like) channel ``j`` is
+  ``0.9 * x[j-1] + sqrt(0.19) * w[j]`` with ``w[j]`` an independent walk;
+* instance: the template resampled by linear interpolation at a random
+  monotone piecewise-linear time warp with 8 segments whose slopes are
+  U[0.5, 1.5] (renormalised to map [0,1] onto [0,1]), plus N(0, sigma^2)
+  noise, sigma = 0.1;
+* queries are fresh instances of random classes.
+
+Series are stored point-major: ``points[off[i]:off[i+1], :]`` is series ``i``
+with shape ``[len_i, d]``, float32.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+N_WARP_SEGMENTS = 8
+
+
+@dataclass
+class Workload:
+    """A database plus a query batch."""
+
+    d: int
+    db: np.ndarray            # [sum(len), d] float32
+    db_off: np.ndarray        # [N+1] int64, point offsets
+    db_labels: np.ndarray     # [N] int32
+    q: np.ndarray             # [sum(qlen), d] float32
+    q_off: np.ndarray         # [Q+1] int64
+    q_labels: np.ndarray      # [Q] int32
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_series(self) -> int:
+        return int(self.db_off.shape[0] - 1)
+
+    @property
+    def n_queries(self) -> int:
+        return int(self.q_off.shape[0] - 1)
+
+    def series(self, i: int) -> np.ndarray:
+        return self.db[self.db_off[i]:self.db_off[i + 1]]
+
+    def query(self, i: int) -> np.ndarray:
+        return self.q[self.q_off[i]:self.q_off[i + 1]]
+
+    def db_lengths(self) -> np.ndarray:
+        return np.diff(self.db_off)
+
+    def q_lengths(self) -> np.ndarray:
+        return np.diff(self.q_off)
+
+
+def _templates(rng: np.random.Generator, n_classes: int, length: int, d: int,
+               correlated: bool) -> np.ndarray:
+    walks = np.cumsum(rng.standard_normal((n_classes, length, d)), axis=1)
+    if not correlated:
+        return walks
+    out = np.empty_like(walks)
+    out[:, :, 0] = walks[:, :, 0]
+    a, b = 0.9, np.sqrt(0.19)
+    for j in range(1, d):
+        out[:, :, j] = a * out[:, :, j - 1] + b * walks[:, :, j]
+    return out
+
+
+def _warp_knots(rng: np.random.Generator, count: int) -> np.ndarray:
+    """Cumulative warp values at the 9 knots of an 8-segment monotone warp."""
+    slopes = rng.uniform(0.5, 1.5, size=(count, N_WARP_SEGMENTS))
+    cum = np.concatenate([np.zeros((count, 1)), np.cumsum(slopes, axis=1)], axis=1)
+    return cum / cum[:, -1:]
+
+
+def _instances(templates: np.ndarray, classes: np.ndarray, knots: np.ndarray,
+               length: int, noise: np.ndarray) -> np.ndarray:
+    """Resample templates[classes] at warped positions; returns [B, length, d]."""
+    B = classes.shape[0]
+    lt = templates.shape[1]
+    u = np.linspace(0.0, 1.0, length) if length > 1 else np.zeros(1)
+    # piecewise-linear warp: knot x positions are uniform in [0,1]
+    seg = np.minimum((u * N_WARP_SEGMENTS).astype(np.int64), N_WARP_SEGMENTS - 1)
+    frac = u * N_WARP_SEGMENTS - seg
+    w = knots[:, seg] * (1.0 - frac) + knots[:, seg + 1] * frac       # [B, length]
+    tau = np.clip(w, 0.0, 1.0) * (lt - 1)
+    i0 = np.minimum(np.floor(tau).astype(np.int64), lt - 2 if lt > 1 else 0)
+    f = (tau - i0)[..., None]
+    t = templates[classes]                                            # [B, lt, d]
+    g0 = np.take_along_axis(t, i0[..., None], axis=1)
+    g1 = np.take_along_axis(t, np.minimum(i0 + 1, lt - 1)[..., None], axis=1)
+    return g0 * (1.0 - f) + g1 * f + noise
+
+
+def make_workload(*, n_series: int, n_queries: int, d: int, length=64,
+                  n_classes: int = 5, seed: int = 0, noise_sigma: float = 0.1,
+                  correlated: bool = False, length_range: Optional[tuple] = None,
+                  template_length: Optional[int] = None,
+                  batch: int = 16384) -> Workload:
+    """Draw a seeded workload.
+
+    ``length`` fixes every series length; ``length_range=(lo, hi)`` draws each
+    length uniformly from the integers in [lo, hi] instead (both database and
+    queries).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lt = template_length or (length_range[1] if length_range else length)
+    templ = _templates(rng, n_classes, lt, d, correlated)
+    total = n_series + n_queries
+    classes = rng.integers(0, n_classes, size=total).astype(np.int32)
+    knots = _warp_knots(rng, total)
+    if length_range is None:
+        lens = np.full(total, int(length), dtype=np.int64)
+    else:
+        lens = rng.integers(length_range[0], length_range[1] + 1, size=total).astype(np.int64)
+    off = np.zeros(total + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    pts = np.empty((int(off[-1]), d), dtype=np.float32)
+    if length_range is None:
+        for s in range(0, total, batch):
+            e = min(total, s + batch)
+            nz = rng.standard_normal((e - s, int(length), d)) * noise_sigma
+            inst = _instances(templ, classes[s:e], knots[s:e], int(length), nz)
+            pts[off[s]:off[e]] = inst.reshape(-1, d).astype(np.float32)
+    else:
+        for s in range(total):
+            n = int(lens[s])
+            nz = rng.standard_normal((1, n, d)) * noise_sigma
+            inst = _instances(templ, classes[s:s + 1], knots[s:s + 1], n, nz)
+            pts[off[s]:off[s + 1]] = inst[0].astype(np.float32)
+    db_end = int(off[n_series])
+    return Workload(
+        d=d,
+        db=pts[:db_end],
+        db_off=off[:n_series + 1].copy(),
+        db_labels=classes[:n_series].copy(),
+        q=pts[db_end:],
+        q_off=off[n_series:] - off[n_series],
+        q_labels=classes[n_series:].copy(),
+        meta=dict(seed=seed, n_classes=n_classes, noise_sigma=noise_sigma,
+                  correlated=correlated, length=length, length_range=length_range),
+    )
+
+
+# Named workloads (sizes of the scan's benchmark configurations).
+WORKLOADS = {
+    # d=2, 1,000 series of length 64, 10 queries, 5 classes, seed 0
+    "tiny_d2_n1k_L64": dict(n_series=1000, n_queries=10, d=2, length=64, n_classes=5, seed=0),
+    # d=3, 100,000 series of length 256, 1,000 queries, 20 classes
+    "scale_d3_n100k_L256": dict(n_series=100_000, n_queries=1000, d=3, length=256,
+                                n_classes=20, seed=1),
+    # 200,000 series, lengths U[50,1000], 256 queries; one data set per d in 3..8
+    **{f"uneven_d{d}_n200k_L50_1000": dict(n_series=200_000, n_queries=256, d=d,
+                                           length_range=(50, 1000), n_classes=20,
+                                           seed=2 + d) for d in range(3, 9)},
+    # d=3, 1,000,000 series of length 128, 1,000 queries, 50 classes
+    "learned_d3_n1M_L128": dict(n_series=1_000_000, n_queries=1000, d=3, length=128,
+                                n_classes=50, seed=3),
+    # d=16 correlated channels (AR(1), rho=0.9), 500,000 series of length 512
+    "highdim_d16_n500k_L512": dict(n_series=500_000, n_queries=1000, d=16, length=512,
+                                   n_classes=50, seed=4, correlated=True),
+}
+
+
+def named(name: str, **overrides) -> Workload:
+    """Build a named workload; ``overrides`` may shrink it (e.g. n_series)."""
+    kw = dict(WORKLOADS[name])
+    kw.update(overrides)
+    return make_workload(**kw)
