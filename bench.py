@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: exact k-NN scan (DTW and DK) on the d=3, 100,000 x 256 workload.
+
+One step = one batched scan of the step's 1,000 queries (per GPU) against the
+100,000-series database, for DTW and for DK (k = 10, Sakoe-Chiba band 10%),
+through the library's public C-ABI, inputs already resident in HBM.  Prints
+one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun (N > 1) every rank scans its own 1,000 queries against a
+replica of the database (independent problems, no data-path collective);
+value = all ranks' queries / the slowest rank's time.
+
+--impl reference times the FP64 oracle (the paper's pruned scan, CPU) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exact k-NN queries/sec and DP GCUPS (DTW & DK), learned+batched vs plain GPU scan"
+WORKLOAD = "scale_d3_n100k_L256"
+N_SERIES, LENGTH, D, N_QUERIES = 100_000, 256, 3, 1000
+K, BAND = 10, 0.1
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        except FileNotFoundError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(world: int):
+    from synthdata import make_workload
+    return make_workload(n_series=N_SERIES, n_queries=N_QUERIES * world, d=D, length=LENGTH,
+                         n_classes=20, seed=1)
+
+
+def cpu_baseline(w, n_sample: int = 4) -> dict:
+    """The FP64 oracle (paper's pruned scan) on a bounded sample of queries."""
+    import oracle
+    oracle.lib()
+    cores = os.cpu_count() or 1
+    band = float(np.float32(BAND))
+    q_off = w.q_off[: n_sample + 1]
+    q = w.q[: q_off[-1]]
+    t0 = time.perf_counter()
+    cells = 0
+    for kind in (0, 1):
+        _, _, st = oracle.knn(w.db, w.db_off, q, q_off, band=band, kind=kind, k=K, method=True,
+                              threads=cores, with_stats=True)
+        cells += int(st[:, 3].sum())
+    dt = time.perf_counter() - t0
+    return {"value": 2 * n_sample / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_sample} queries x {N_SERIES} series, DTW and DK, k={K}, band 10%, "
+                      f"FP64 pruned scan (LB_Box, GDK, sparse DK, early abandoning), "
+                      f"{cores} threads",
+            "seconds": dt, "dp_cells": cells}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(1)
+    n_sample = 2
+    for _ in range(args.warmup):
+        cpu_baseline(w, n_sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_baseline(w, n_sample)
+    dt = time.perf_counter() - t0
+    value = 2 * n_sample * args.steps / dt
+    cores = os.cpu_count() or 1
+    sample = f"{n_sample} queries x {N_SERIES} series per step, DTW and DK, k={K}, band 10%"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH, "d": D,
+                       "k": K, "band": BAND, "sample_queries_per_step": n_sample},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_1811_11076_gb300 as kw
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    kw.lib()
+
+    w = workload(world)
+    q0, q1 = w.q_off[rank * N_QUERIES], w.q_off[(rank + 1) * N_QUERIES]
+    q_host = np.ascontiguousarray(w.q[q0:q1])
+    q_off = w.q_off[rank * N_QUERIES:(rank + 1) * N_QUERIES + 1] - q0
+    db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
+    q_dev = torch.from_numpy(q_host).cuda()
+    q_off_t = torch.from_numpy(q_off)
+    ids = torch.empty((N_QUERIES, K), dtype=torch.int64, device="cuda")
+    dst = torch.empty((N_QUERIES, K), dtype=torch.float32, device="cuda")
+    cnt = torch.empty(N_QUERIES, dtype=torch.int64, device="cuda")
+    kinds = (kw.DTW, kw.DK)
+
+    def step(collect=None):
+        for kind in kinds:
+            _, _, st = db.scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=kw.SEED_GREEDY,
+                               out=(ids, dst, cnt), stats=True, profile=True)
+            if collect is not None:
+                collect.append((kind, st))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    collected = []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(collected)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_queries = N_QUERIES * len(kinds) * args.steps * world
+    value = total_queries / (ms / 1000.0)
+
+    # per-distance detail (this rank)
+    detail = {}
+    for kind in kinds:
+        sts = [s for k_, s in collected if k_ == kind]
+        agg = {key: sum(s[key] for s in sts) for key in sts[0]}
+        name = "DTW" if kind == kw.DTW else "DK"
+        detail[name] = {
+            "queries_per_s": N_QUERIES * len(sts) / (agg["ms_total"] / 1000.0),
+            "dp_gcups": agg["dp_cells"] / (agg["ms_dp"] / 1000.0) / 1e9 if agg["ms_dp"] else None,
+            "ms_per_scan": agg["ms_total"] / len(sts),
+            "ms_seed": agg["ms_seed"] / len(sts), "ms_lb": agg["ms_lb"] / len(sts),
+            "ms_dp": agg["ms_dp"] / len(sts), "ms_finalize": agg["ms_finalize"] / len(sts),
+            "dp_calls_per_query": agg["dp_calls"] / (N_QUERIES * len(sts)),
+            "dp_abandoned_frac": agg["dp_abandoned"] / max(agg["dp_calls"], 1),
+            "lb_pruned_frac": (agg["lb_pruned"] + agg["lb_pruned_late"]) / max(agg["pairs"], 1),
+            "dp_cells_per_query": agg["dp_cells"] / (N_QUERIES * len(sts)),
+            "reranked": agg["reranked"],
+        }
+    launches = sum(s["launches"] for _, s in collected)
+
+    # roofline of the dominant kernel (largest share of stage time)
+    hbm_gbs, sm_max_mhz, peak_src = peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    stage = {"seed": 0.0, "lb": 0.0, "dp": 0.0, "finalize": 0.0}
+    cells = {kind: 0 for kind in kinds}
+    lb_bytes = 0
+    for kind, s in collected:
+        for k_ in stage:
+            stage[k_] += s[f"ms_{k_}"]
+        cells[kind] += s["dp_cells"]
+        lb_bytes += s["pairs"] * LENGTH * D * 4
+    dominant = max(stage, key=stage.get)
+    clocks = clk.summary()
+    if dominant == "lb":
+        achieved = lb_bytes / (stage["lb"] / 1000.0) / 1e9
+        roof = {"kernel": "lb_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_gbs,
+                "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        # algorithmic work of the DP: 2d+3 FP32 lane operations per band cell
+        ops = sum(cells.values()) * (2 * D + 3)
+        achieved = ops / (stage["dp"] / 1000.0) / 1e12
+        peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
+        roof = {"kernel": "dp_kernel" if dominant == "dp" else dominant, "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 lane ops)",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
+                               f"(max SM clock, {peak_src})",
+                "stage_share": {k_: v / sum(stage.values()) for k_, v in stage.items()}}
+        if clocks.get("sm_mhz"):
+            roof["frac_at_sampled_clock"] = achieved / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    # end to end through the public API with host buffers: H2D of queries and
+    # D2H of results inside the timed region
+    q_pin = torch.from_numpy(q_host).pin_memory()
+    ids_h = torch.empty((N_QUERIES, K), dtype=torch.int64).pin_memory()
+    dst_h = torch.empty((N_QUERIES, K), dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty(N_QUERIES, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for kind in kinds:
+            db.scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, out=(ids_h, dst_h, cnt_h))
+    barrier()
+    e2e_dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    h2d = (q_host.nbytes + q_off.nbytes) * len(kinds)
+    d2h = (ids_h.numel() * 8 + dst_h.numel() * 4 + cnt_h.numel() * 8) * len(kinds)
+    e2e = {"value": N_QUERIES * len(kinds) * e2e_steps * world / e2e_dt, "unit": "queries/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # the plain form: one query per launch sequence, first 50 queries
+    plain = {}
+    if rank == 0:
+        nplain = 50
+        qp = q_dev[: int(q_off[nplain])]
+        qpo = q_off_t[: nplain + 1]
+        for kind in kinds:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            db.scan(qp, qpo, k=K, band=BAND, distance=kind, query_batch=1)
+            torch.cuda.synchronize()
+            plain["DTW" if kind == kw.DTW else "DK"] = nplain / (time.perf_counter() - t0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH, "d": D,
+                       "queries_per_gpu": N_QUERIES, "k": K, "band": BAND,
+                       "distances": ["DTW", "DK"], "seed": "greedy upper bound (Section 4.3)",
+                       "batched": True, "l2": "inputs larger than L2 (307 MB database)",
+                       "parallelism": f"replicated database, queries sharded x{world}"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+            "per_distance": detail, "plain_scan_queries_per_s": plain,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+        print(json.dumps(line), flush=True)
+    db.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

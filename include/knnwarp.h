@@ -1,0 +1,215 @@
+/*
+ * knnwarp: exact k-NN / eps-NN scan of multi-dimensional time series under
+ * Sakoe-Chiba-banded DTW and the dog-keeper distance DK, for NVIDIA GB300
+ * (sm_103a).
+ *
+ * Method: Bachmann & Freytag, "An Analytical Approach to Improving Time
+ * Warping on Multidimensional Time Series" (arXiv 1811.11076).
+ *   - DTW and DK definitions: Section 2.1; band: Section 2.2.
+ *   - Envelope / LB_Keogh: Section 2.3; LB_Box: Section 3, Eq. 1.
+ *   - GDK upper bound: Section 4.1, Algorithm 1.
+ *   - Threshold-driven (sparse) DK: Section 4.2, Algorithm 3.
+ *   - Nearest-neighbour search with an upper-bound pre-pass: Section 4.3.
+ *   - k-NN and eps-NN query semantics: Section 1.
+ *
+ * Conventions shared by every entry point
+ *   - Series are point-major FP32: a series of length n in d dimensions is
+ *     n*d consecutive floats (point i, coordinate j at [i*d + j]).  A set of
+ *     series is concatenated; offsets[s] .. offsets[s+1] are its points.
+ *   - Band: r = floor(band * max(m, n)) for lengths m, n; band >= 1 means no
+ *     constraint.  A pair with |m - n| > r has distance +inf and is never
+ *     returned.
+ *   - Units: DTW is the SUM of squared Euclidean point costs along the best
+ *     path (no final root), DK the Euclidean max along the best path.
+ *   - Results are ordered by (distance, id) ascending; ids are the caller's
+ *     0-based series indices.  k-NN rows with fewer than k finite results are
+ *     padded with id -1 and distance +inf.
+ *   - Exactness: id sets equal those of an FP64 evaluation; candidates whose
+ *     FP32 distance lies within the FP32 error band of the boundary are
+ *     re-scored in FP64 on the device before the cut.
+ *   - Memory: unless stated otherwise a pointer argument may be host memory
+ *     (pageable or pinned) or device memory of the current device; the
+ *     library detects the kind and stages host buffers itself.  Callers keep
+ *     ownership of everything they pass in.  Library objects (knn_db,
+ *     knn_encoder) are owned by the library until their destroy call.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Every call is synchronous with respect to its outputs: when it returns,
+ *     outputs are written and the status is final.
+ *   - Errors: every call returns a knn_status; nothing aborts the process,
+ *     throws across the boundary or traps on the device.  Invalid arguments
+ *     are rejected before any launch.  knn_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.
+ *   - Thread safety: distinct knn_db objects may be used concurrently; one
+ *     knn_db must not be used by two calls at the same time.
+ */
+#ifndef KNNWARP_H
+#define KNNWARP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KNN_API __attribute__((visibility("default")))
+
+typedef enum { KNN_DTW = 0, KNN_DK = 1 } knn_distance;
+
+typedef enum {
+    KNN_OK = 0,
+    KNN_ERR_INVALID = 1,     /* bad argument (detected before any launch)        */
+    KNN_ERR_OOM = 2,         /* device allocation failed                         */
+    KNN_ERR_CUDA = 3,        /* a CUDA call failed                               */
+    KNN_ERR_TIMEOUT = 4,     /* a bounded device wait gave up                    */
+    KNN_ERR_CAPACITY = 5,    /* eps-NN result larger than eps_capacity; counts
+                                hold the true sizes                              */
+    KNN_ERR_UNSUPPORTED = 6  /* configuration not compiled in (e.g. d > 16)     */
+} knn_status;
+
+/* How the running threshold is seeded before the pruned scan. */
+typedef enum {
+    /* Section 4.3: an upper bound for every series from the greedy path of
+     * Algorithm 1 (max of costs for DK = GDK; sum of squared costs for DTW);
+     * the k-th smallest becomes the initial threshold. */
+    KNN_SEED_GREEDY = 0,
+    /* Learned proposal: the attached encoder ranks the series by predicted
+     * distance, the seed_count best are scored exactly first, and the k-th
+     * best exact distance becomes the initial threshold.  Needs an encoder
+     * attached to the database (knn_encoder_attach). */
+    KNN_SEED_LEARNED = 1,
+    /* No pre-pass: the threshold starts at +inf. */
+    KNN_SEED_NONE = 2
+} knn_seed_mode;
+
+typedef struct {
+    int32_t k;             /* > 0: k-NN with this k; 0: eps-NN                      */
+    float eps;             /* eps-NN radius in output units (ignored for k-NN)      */
+    float band;            /* Sakoe-Chiba band as a fraction of max(m, n), > 0       */
+    int32_t distance;      /* knn_distance                                           */
+    int32_t seed_mode;     /* knn_seed_mode                                          */
+    int32_t seed_count;    /* learned seeding: proposals scored exactly first
+                              (0 = 4 * k, at least 64)                               */
+    int32_t query_batch;   /* queries per launch sequence; 0 = all in one batch      */
+    int32_t use_graph;     /* 1 = capture each batch's launch sequence in a CUDA
+                              graph and replay it (cached per database and shape)    */
+    int64_t eps_capacity;  /* eps-NN: result slots per query                         */
+    int32_t profile;       /* 1 = time each stage with CUDA events (stats->ms_*);
+                              ignored when use_graph = 1                             */
+    int32_t reserved;
+} knn_params;
+
+/* Counters of one scan (summed over queries).  Cells are DP cells actually
+ * evaluated, counted up to the point where a candidate was abandoned. */
+typedef struct {
+    int64_t pairs;           /* (query, series) pairs considered                 */
+    int64_t band_infeasible; /* pairs with |m - n| > r                           */
+    int64_t ub_walks;        /* greedy upper-bound walks run                     */
+    int64_t seeds;           /* learned proposals scored exactly                 */
+    int64_t lb_pruned;       /* pruned by LB_Box before the DP queue             */
+    int64_t lb_pruned_late;  /* pruned by LB_Box at DP start (tighter threshold) */
+    int64_t dp_calls;        /* dynamic programs started                         */
+    int64_t dp_abandoned;    /* dynamic programs abandoned early                 */
+    int64_t dp_cells;        /* band cells evaluated (lane slots x steps)        */
+    int64_t reranked;        /* candidates re-scored in FP64                     */
+    int64_t launches;        /* kernels launched by the call                     */
+    double ms_total;         /* time of the call on the stream                   */
+    double ms_seed;          /* profile = 1: threshold seeding (greedy/learned)  */
+    double ms_lb;            /* profile = 1: envelopes + LB_Box stream           */
+    double ms_dp;            /* profile = 1: banded dynamic programs             */
+    double ms_finalize;      /* profile = 1: FP64 re-scoring and output          */
+} knn_stats;
+
+typedef struct knn_db knn_db;
+typedef struct knn_encoder knn_encoder;
+
+/* ---------------------------------------------------------------------- */
+/* Database                                                                 */
+
+/* Copy n_series series (concatenated `series`, `offsets` with n_series+1
+ * entries in points) into a library-owned device layout: series grouped
+ * into length buckets, each series starting on a 16-byte boundary and padded
+ * to a whole number of LB chunks.  1 <= d <= 16; every length >= 1. */
+KNN_API knn_status knn_db_create(const float *series, const int64_t *offsets,
+                                 int64_t n_series, int32_t d, void *stream,
+                                 knn_db **out);
+KNN_API knn_status knn_db_destroy(knn_db *db);
+/* Number of series and dimensionality. */
+KNN_API knn_status knn_db_info(const knn_db *db, int64_t *n_series, int32_t *d,
+                               int32_t *n_buckets);
+
+/* ---------------------------------------------------------------------- */
+/* Scan                                                                     */
+
+/* Exact k-NN (params->k > 0) or eps-NN (params->k == 0) of n_queries queries
+ * against the database (Section 1 semantics; method of Sections 2-4).
+ *   queries, q_offsets: as `series`/`offsets` above (q_offsets has
+ *     n_queries+1 entries), same d as the database.
+ *   k-NN:   out_ids [n_queries][k], out_dist [n_queries][k]; out_counts may
+ *           be NULL (else receives the number of finite results per query).
+ *   eps-NN: out_ids/out_dist [n_queries][eps_capacity], out_counts
+ *           [n_queries] (true result sizes; KNN_ERR_CAPACITY if one exceeds
+ *           eps_capacity, with the first eps_capacity results written).
+ *   stats may be NULL. */
+KNN_API knn_status knn_scan(knn_db *db, const float *queries, const int64_t *q_offsets,
+                            int32_t n_queries, const knn_params *params,
+                            int64_t *out_ids, float *out_dist, int64_t *out_counts,
+                            knn_stats *stats, void *stream);
+
+/* One query against series given as a flat array with lengths (the
+ * knn_scan(query, db, lengths, d, band, k|eps, distance) form).  k > 0: k-NN
+ * (ids/dist hold k entries); k == 0: eps-NN (ids/dist hold n_series
+ * entries; *count receives the result size).  Builds a temporary database. */
+KNN_API knn_status knn_scan_simple(const float *query, int64_t m, const float *db,
+                                   const int64_t *lengths, int64_t n_series, int32_t d,
+                                   float band, int32_t k, float eps, int32_t distance,
+                                   int64_t *ids, float *dist, int64_t *count);
+
+/* ---------------------------------------------------------------------- */
+/* Components (each is one step of the scan, exposed for verification and  */
+/* for callers who build their own pipelines).  All pointers device memory. */
+
+/* Envelope of one series (Section 2.3; per dimension, Section 3): for
+ * i in [0, len) and coordinate j, lo[i*d+j] = min of t[p*d+j] over
+ * |p - i| <= r, 0 <= p < n, hi likewise with max; +inf/-inf where the window
+ * is empty.  Outputs are [len][d]. */
+KNN_API knn_status knn_envelope(const float *t, int64_t n, int32_t d, int64_t r,
+                                int64_t len, float *lo, float *hi, void *stream);
+
+/* LB_Box of every database series against the envelope of `query`
+ * (Section 3, Eq. 1, with the envelope on the query side; banded DTW is
+ * symmetric).  form 0: sum over points of the squared box distance (bounds
+ * DTW); form 1: max over points (bounds DK^2).  out_lb[n_series] in the
+ * caller's series order; band-infeasible series get +inf. */
+KNN_API knn_status knn_lb_box(knn_db *db, const float *query, int64_t m, float band,
+                              int32_t form, float *out_lb, void *stream);
+
+/* Greedy upper bound of every database series (Section 4.1, Algorithm 1,
+ * walked to the end cell): form 0 = GDK (max of Euclidean costs), form 1 =
+ * sum of squared costs along the same path (bounds DTW).  out_ub[n_series]
+ * in the caller's series order. */
+KNN_API knn_status knn_greedy_ub(knn_db *db, const float *query, int64_t m, float band,
+                                 int32_t form, float *out_ub, void *stream);
+
+/* Banded DTW / DK of explicit pairs (a[pa[i]], b[pb[i]]) with no pruning
+ * (Section 2.1).  a_off/b_off: point offsets (device, int64).  Writes FP32
+ * results to out_f32 (nullable) and FP64 results to out_f64 (nullable,
+ * computed by a separate FP64 program). */
+KNN_API knn_status knn_pairwise(const float *a, const int64_t *a_off, const float *b,
+                                const int64_t *b_off, const int64_t *pa, const int64_t *pb,
+                                int64_t n_pairs, int32_t d, float band, int32_t distance,
+                                float *out_f32, double *out_f64, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Diagnostics                                                              */
+
+KNN_API const char *knn_status_string(knn_status s);
+/* Thread-local description of the last error on this thread ("" if none). */
+KNN_API const char *knn_last_error(void);
+/* Library version string. */
+KNN_API const char *knn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNNWARP_H */

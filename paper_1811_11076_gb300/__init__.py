@@ -1,0 +1,278 @@
+"""Exact k-NN / eps-NN scan of multi-dimensional time series under banded DTW
+and the dog-keeper distance DK, on NVIDIA GB300 (sm_103a).
+
+Method: Bachmann & Freytag, "An Analytical Approach to Improving Time Warping
+on Multidimensional Time Series" (arXiv 1811.11076): LB_Box pruning
+(Section 3, Eq. 1), GDK upper bounds (Section 4.1, Algorithm 1),
+threshold-driven DK (Section 4.2, Algorithm 3), nearest-neighbour search with
+an upper-bound pre-pass (Section 4.3).
+
+This module only marshals arguments to the C-ABI of ``libknnwarp.so``
+(declared in ``include/knnwarp.h``); every step of the scan runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library has not
+been built, importing works but every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libknnwarp.so")
+
+DTW = 0
+DK = 1
+SEED_GREEDY = 0
+SEED_LEARNED = 1
+SEED_NONE = 2
+
+STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA",
+          4: "KNN_ERR_TIMEOUT", 5: "KNN_ERR_CAPACITY", 6: "KNN_ERR_UNSUPPORTED"}
+
+# every symbol include/knnwarp.h declares
+EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
+           "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
+           "knn_last_error", "knn_version")
+
+
+class KnnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("eps", C.c_float), ("band", C.c_float),
+                ("distance", C.c_int32), ("seed_mode", C.c_int32), ("seed_count", C.c_int32),
+                ("query_batch", C.c_int32), ("use_graph", C.c_int32),
+                ("eps_capacity", C.c_int64), ("profile", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("pairs", C.c_int64), ("band_infeasible", C.c_int64), ("ub_walks", C.c_int64),
+                ("seeds", C.c_int64), ("lb_pruned", C.c_int64), ("lb_pruned_late", C.c_int64),
+                ("dp_calls", C.c_int64), ("dp_abandoned", C.c_int64), ("dp_cells", C.c_int64),
+                ("reranked", C.c_int64), ("launches", C.c_int64), ("ms_total", C.c_double),
+                ("ms_seed", C.c_double), ("ms_lb", C.c_double), ("ms_dp", C.c_double),
+                ("ms_finalize", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libknnwarp.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1811_11076_gb300.build` (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    vp, i64p = C.c_void_p, C.c_void_p
+    L.knn_db_create.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(vp)]
+    L.knn_db_destroy.argtypes = [vp]
+    L.knn_db_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                              C.POINTER(C.c_int32)]
+    L.knn_scan.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(Params), vp, vp, vp,
+                           C.POINTER(Stats), vp]
+    L.knn_scan_simple.argtypes = [vp, C.c_int64, vp, vp, C.c_int64, C.c_int32, C.c_float,
+                                  C.c_int32, C.c_float, C.c_int32, vp, vp,
+                                  C.POINTER(C.c_int64)]
+    L.knn_envelope.argtypes = [vp, C.c_int64, C.c_int32, C.c_int64, C.c_int64, vp, vp, vp]
+    L.knn_lb_box.argtypes = [vp, vp, C.c_int64, C.c_float, C.c_int32, vp, vp]
+    L.knn_greedy_ub.argtypes = [vp, vp, C.c_int64, C.c_float, C.c_int32, vp, vp]
+    L.knn_pairwise.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_float,
+                               C.c_int32, vp, vp, vp]
+    for f in EXPORTS:
+        if f not in ("knn_status_string", "knn_last_error", "knn_version"):
+            getattr(L, f).restype = C.c_int
+    L.knn_status_string.restype = C.c_char_p
+    L.knn_status_string.argtypes = [C.c_int]
+    L.knn_last_error.restype = C.c_char_p
+    L.knn_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise KnnError(status, lib().knn_last_error().decode())
+
+
+def _ptr(x) -> int:
+    """Address of a torch tensor or numpy array (contiguous)."""
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+def _stream(stream=None) -> int:
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def _f32(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        return a.to(torch.float32).contiguous()
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i64(a):
+    if hasattr(a, "data_ptr"):
+        import torch
+        return a.to(torch.int64).contiguous()
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+class KnnDB:
+    """A database of series in the library's device layout (knn_db)."""
+
+    def __init__(self, series, offsets, d: int | None = None, stream=None):
+        series = _f32(series)
+        offsets = _i64(offsets)
+        if d is None:
+            d = int(series.shape[1]) if len(series.shape) == 2 else 1
+        h = C.c_void_p()
+        self._keep = (series, offsets)
+        _check(lib().knn_db_create(_ptr(series), _ptr(offsets), int(offsets.shape[0] - 1), int(d),
+                                   _stream(stream), C.byref(h)))
+        self._h = h
+        self._keep = None
+        self.d = int(d)
+        self.n = int(offsets.shape[0] - 1)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        n, d, b = C.c_int64(), C.c_int32(), C.c_int32()
+        _check(lib().knn_db_info(self._h, C.byref(n), C.byref(d), C.byref(b)))
+        return {"n_series": n.value, "d": d.value, "n_buckets": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().knn_db_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def scan(self, queries, q_offsets, *, k: int = 1, eps: float = 0.0, band: float = 0.1,
+             distance: int = DTW, seed: int = SEED_GREEDY, seed_count: int = 0,
+             query_batch: int = 0, use_graph: bool = False, eps_capacity: int = 0,
+             out=None, stream=None, stats: bool = False, profile: bool = False):
+        """Exact k-NN (k > 0) or eps-NN (k == 0).  Inputs and outputs may be
+        host (numpy / CPU tensors) or device (CUDA tensors).  Returns
+        (ids, dist) for k-NN, (ids, dist, counts) for eps-NN, plus a stats
+        dict if requested."""
+        queries = _f32(queries)
+        q_offsets = _i64(q_offsets)
+        nq = int(q_offsets.shape[0] - 1)
+        width = k if k > 0 else eps_capacity
+        if out is None:
+            dev = hasattr(queries, "is_cuda") and queries.is_cuda
+            if dev:
+                import torch
+                ids = torch.empty((nq, width), dtype=torch.int64, device=queries.device)
+                dist = torch.empty((nq, width), dtype=torch.float32, device=queries.device)
+                counts = torch.empty(nq, dtype=torch.int64, device=queries.device)
+            else:
+                ids = np.empty((nq, width), dtype=np.int64)
+                dist = np.empty((nq, width), dtype=np.float32)
+                counts = np.empty(nq, dtype=np.int64)
+        else:
+            ids, dist, counts = out
+        p = Params(k=k, eps=eps, band=band, distance=distance, seed_mode=seed,
+                   seed_count=seed_count, query_batch=query_batch, use_graph=int(use_graph),
+                   eps_capacity=eps_capacity, profile=int(profile))
+        st = Stats()
+        _check(lib().knn_scan(self._h, _ptr(queries), _ptr(q_offsets), nq, C.byref(p), _ptr(ids),
+                              _ptr(dist), _ptr(counts), C.byref(st), _stream(stream)))
+        res = (ids, dist) if k > 0 else (ids, dist, counts)
+        return res + (st.as_dict(),) if stats else res
+
+    def lb_box(self, query, band: float, form: int = 0, stream=None):
+        """LB_Box of every series against the query envelope (device tensor out)."""
+        import torch
+        query = _f32(query)
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        _check(lib().knn_lb_box(self._h, _ptr(query), int(query.shape[0]), band, form, _ptr(out),
+                                _stream(stream)))
+        return out
+
+    def greedy_ub(self, query, band: float, form: int = 0, stream=None):
+        """Greedy (Algorithm 1) upper bound of every series (device tensor out)."""
+        import torch
+        query = _f32(query)
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        _check(lib().knn_greedy_ub(self._h, _ptr(query), int(query.shape[0]), band, form,
+                                   _ptr(out), _stream(stream)))
+        return out
+
+
+def envelope(t, r: int, length: int | None = None, stream=None):
+    """Band envelope (lo, hi) of a device series t [n, d] (Sections 2.3, 3)."""
+    import torch
+    t = _f32(t)
+    n, d = int(t.shape[0]), int(t.shape[1])
+    length = n if length is None else length
+    lo = torch.empty((length, d), dtype=torch.float32, device=t.device)
+    hi = torch.empty((length, d), dtype=torch.float32, device=t.device)
+    _check(lib().knn_envelope(_ptr(t), n, d, r, length, _ptr(lo), _ptr(hi), _stream(stream)))
+    return lo, hi
+
+
+def pairwise(a, a_off, b, b_off, pa, pb, *, band: float, distance: int, fp64: bool = False,
+             fp32: bool = True, stream=None):
+    """Banded DTW/DK of pairs (a[pa[i]], b[pb[i]]); device tensors in and out."""
+    import torch
+    a, b = _f32(a), _f32(b)
+    a_off, b_off, pa, pb = _i64(a_off), _i64(b_off), _i64(pa), _i64(pb)
+    n = int(pa.shape[0])
+    d = int(a.shape[1])
+    o32 = torch.empty(n, dtype=torch.float32, device=a.device) if fp32 else None
+    o64 = torch.empty(n, dtype=torch.float64, device=a.device) if fp64 else None
+    _check(lib().knn_pairwise(_ptr(a), _ptr(a_off), _ptr(b), _ptr(b_off), _ptr(pa), _ptr(pb), n,
+                              d, band, distance, _ptr(o32) if fp32 else None,
+                              _ptr(o64) if fp64 else None, _stream(stream)))
+    return o32, o64
+
+
+def scan_simple(query, db, lengths, *, d: int, band: float, k: int = 1, eps: float = 0.0,
+                distance: int = DTW):
+    """knn_scan(query, db, lengths, d, band, k|eps, distance) -> ids, distances."""
+    query = _f32(query)
+    db = _f32(db)
+    lengths = _i64(lengths)
+    n = int(lengths.shape[0])
+    width = k if k > 0 else min(n, 8192)
+    ids = np.empty(width, dtype=np.int64)
+    dist = np.empty(width, dtype=np.float32)
+    cnt = C.c_int64(0)
+    _check(lib().knn_scan_simple(_ptr(query), int(query.shape[0]), _ptr(db), _ptr(lengths), n, d,
+                                 band, k, eps, distance, _ptr(ids), _ptr(dist), C.byref(cnt)))
+    if k > 0:
+        return ids, dist
+    c = min(cnt.value, width)
+    return ids[:c], dist[:c]

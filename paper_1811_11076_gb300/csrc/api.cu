@@ -1,0 +1,364 @@
+// C-ABI of the scan library: database layout, scan orchestration, components.
+//
+// Launch sequence of one query batch (all on the caller's stream, no host
+// synchronisation between launches, so the whole sequence can be captured
+// into a CUDA graph):
+//   repack queries -> init thresholds/slots -> [greedy upper bounds per bucket]
+//   -> per bucket: envelope, LB_Box stream (prune + survivor queue)
+//   -> DP over the survivor queue -> finalise (FP64 boundary re-scoring, cut)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/knnwarp.h"
+#include "common.cuh"
+#include "internal.h"
+#include "runtime.h"
+
+using namespace knn;
+
+// ---------------------------------------------------------------------------
+// errors
+
+static thread_local std::string g_err;
+
+knn_status knn::set_error(knn_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+knn_status knn::cuda_error(cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear sticky-free errors
+    return set_error(e == cudaErrorMemoryAllocation ? KNN_ERR_OOM : KNN_ERR_CUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" const char *knn_status_string(knn_status s)
+{
+    switch (s) {
+    case KNN_OK: return "ok";
+    case KNN_ERR_INVALID: return "invalid argument";
+    case KNN_ERR_OOM: return "out of device memory";
+    case KNN_ERR_CUDA: return "CUDA error";
+    case KNN_ERR_TIMEOUT: return "device wait timed out";
+    case KNN_ERR_CAPACITY: return "result capacity exceeded";
+    case KNN_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *knn_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *knn_version(void) { return "knnwarp 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// helpers
+
+int knn::deff_for(int d)
+{
+    if (d >= 1 && d <= 8)
+        return d;
+    if (d <= 16)
+        return 16;
+    return 0;
+}
+
+bool knn::is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+knn_status DevBuf::ensure(size_t b)
+{
+    if (b <= bytes)
+        return KNN_OK;
+    release();
+    if (const char *f = getenv("KNN_FAULT_INJECT"))
+        if (!strcmp(f, "alloc"))
+            return set_error(KNN_ERR_OOM, "allocation failure injected (KNN_FAULT_INJECT=alloc)");
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return cuda_error(e, "cudaMalloc");
+    }
+    bytes = b;
+    return KNN_OK;
+}
+
+void DevBuf::release()
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+Margins knn::margins_for(int kind, int max_path, int d)
+{
+    const double u = std::ldexp(1.0, -24);
+    double w;
+    if (kind == 0)
+        w = 2.0 * (max_path + d + 8) * u;  // DTW: sum along a path of <= m+n-1 cells
+    else
+        w = 2.0 * (d + 8) * u;             // DK: one cost of d terms, then max/min only
+    Margins g;
+    g.rerank_rel = (float)w;
+    g.mu_keep = (float)(1.0 + w);
+    g.mu_prune = (float)(1.0 + 3.0 * w);
+    return g;
+}
+
+static int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v)
+        p <<= 1;
+    return p;
+}
+
+// Default (P, G) for a band radius r: minimise the modelled lane work
+// G * (n + P + 1) * (2P(2d+3) + overhead) subject to G*P >= r+1, G <= 32.
+void knn::choose_dp_config(int deff, int r, int n, int *P_out, int *G_out)
+{
+    double best = 1e300;
+    int bp = 0, bg = 0;
+    const int nv = dp_num_variants(deff);
+    for (int v = 0; v < nv; ++v) {
+        const int P = dp_variant_P(deff, v);
+        int G = next_pow2((r + 1 + P - 1) / P);
+        if (G < 1)
+            G = 1;
+        if (G > 32)
+            continue;
+        const double per_step = 2.0 * P * (2 * deff + 3) + 16.0 + 2.0 * deff;
+        const double cost = (double)G * (n + P + 1) * per_step;
+        if (cost < best) {
+            best = cost;
+            bp = P;
+            bg = G;
+        }
+    }
+    *P_out = bp;
+    *G_out = bg;
+}
+
+// ---------------------------------------------------------------------------
+// database
+
+__global__ void check_finite_kernel(const float *p, int64_t n, int *flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(p[i])) {
+            *flag = 1;
+            return;
+        }
+}
+
+knn_status knn::check_finite_dev(const float *dev, int64_t n, int *flag_dev, cudaStream_t st,
+                               bool *ok)
+{
+    cudaError_t e = cudaMemsetAsync(flag_dev, 0, sizeof(int), st);
+    if (e != cudaSuccess)
+        return cuda_error(e, "cudaMemsetAsync");
+    if (n > 0) {
+        int64_t b = (n + 255) / 256;
+        check_finite_kernel<<<(int)std::min<int64_t>(b, 4096), 256, 0, st>>>(dev, n, flag_dev);
+    }
+    int h = 0;
+    e = cudaMemcpyAsync(&h, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_error(e, "finite check");
+    *ok = h == 0;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets, int64_t n_series,
+                                    int32_t d, void *stream, knn_db **out)
+{
+    if (!out)
+        return set_error(KNN_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!series || !offsets)
+        return set_error(KNN_ERR_INVALID, "series/offsets is NULL");
+    if (n_series < 1 || n_series > (int64_t)0x7fffffff)
+        return set_error(KNN_ERR_INVALID, "n_series must be in [1, 2^31)");
+    if (d < 1 || d > 16)
+        return set_error(KNN_ERR_INVALID, "d must be in [1, 16]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int deff = deff_for(d);
+    const int CH = chunk_floats(deff), PPC = chunk_points(deff);
+
+    std::vector<int64_t> hoff(n_series + 1);
+    const bool off_dev = is_device_ptr(offsets);
+    if (off_dev) {
+        cudaError_t e = cudaMemcpy(hoff.data(), offsets, sizeof(int64_t) * (n_series + 1),
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return cuda_error(e, "copy offsets");
+    } else {
+        memcpy(hoff.data(), offsets, sizeof(int64_t) * (n_series + 1));
+    }
+    if (hoff[0] < 0)
+        return set_error(KNN_ERR_INVALID, "offsets[0] < 0");
+    int max_len = 0;
+    for (int64_t i = 0; i < n_series; ++i) {
+        const int64_t L = hoff[i + 1] - hoff[i];
+        if (L < 1)
+            return set_error(KNN_ERR_INVALID, "series " + std::to_string(i) + " has length < 1");
+        if (L > 65536)
+            return set_error(KNN_ERR_UNSUPPORTED, "series longer than 65536 points");
+        max_len = std::max<int>(max_len, (int)L);
+    }
+    const int N = (int)n_series;
+
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+        lb_init_attributes();
+        fin_init_attributes();
+    });
+    auto db = new knn_db();
+    db->d = d;
+    db->deff = deff;
+    db->N = N;
+    cudaGetDevice(&db->dev);
+    cudaDeviceGetAttribute(&db->n_sm, cudaDevAttrMultiProcessorCount, db->dev);
+    db->max_len = max_len;
+
+    // length buckets: stable sort by length, a new bucket whenever the length
+    // exceeds the bucket's shortest by more than the bucket width
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return hoff[a + 1] - hoff[a] < hoff[b + 1] - hoff[b];
+    });
+    db->h_len.resize(N);
+    db->h_len_by_id.resize(N);
+    std::vector<int64_t> doff(N), doff_by_id(N);
+    int64_t total = 0;
+    for (int c = 0; c < N; ++c) {
+        const int id = order[c];
+        const int n = (int)(hoff[id + 1] - hoff[id]);
+        db->h_len[c] = n;
+        db->h_len_by_id[id] = n;
+        doff[c] = total;
+        doff_by_id[id] = total;
+        total += (int64_t)((n + PPC - 1) / PPC) * CH;
+    }
+    db->total_floats = total;
+    for (int c = 0; c < N;) {
+        Bucket b;
+        b.c_begin = c;
+        b.n_lo = db->h_len[c];
+        const int width = std::max(16, b.n_lo / 16);
+        while (c < N && db->h_len[c] <= b.n_lo + width)
+            ++c;
+        b.c_end = c;
+        b.n_hi = db->h_len[c - 1];
+        db->buckets.push_back(b);
+    }
+
+    knn_status s;
+    if ((s = db->data.ensure(sizeof(float) * total)) ||
+        (s = db->off.ensure(sizeof(int64_t) * N)) || (s = db->len.ensure(sizeof(int) * N)) ||
+        (s = db->id.ensure(sizeof(int) * N)) || (s = db->off_by_id.ensure(sizeof(int64_t) * N)) ||
+        (s = db->len_by_id.ensure(sizeof(int) * N))) {
+        delete db;
+        return s;
+    }
+    cudaError_t e = cudaSuccess;
+    auto cpy = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    cpy(db->off.p, doff.data(), sizeof(int64_t) * N);
+    cpy(db->len.p, db->h_len.data(), sizeof(int) * N);
+    cpy(db->id.p, order.data(), sizeof(int) * N);
+    cpy(db->off_by_id.p, doff_by_id.data(), sizeof(int64_t) * N);
+    cpy(db->len_by_id.p, db->h_len_by_id.data(), sizeof(int) * N);
+
+    // source series and offsets on the device
+    DevBuf src_stage, off_stage;
+    const float *src = series;
+    const int64_t npts = hoff[n_series];
+    if (!is_device_ptr(series)) {
+        if ((s = src_stage.ensure(sizeof(float) * npts * d))) {
+            delete db;
+            return s;
+        }
+        cpy(src_stage.p, series, sizeof(float) * npts * d);
+        src = (const float *)src_stage.p;
+    }
+    if ((s = off_stage.ensure(sizeof(int64_t) * (n_series + 1)))) {
+        delete db;
+        return s;
+    }
+    cpy(off_stage.p, hoff.data(), sizeof(int64_t) * (n_series + 1));
+    if (e != cudaSuccess) {
+        delete db;
+        return cuda_error(e, "copy database");
+    }
+    if ((s = db->ws.ctrl.ensure(4096))) {
+        delete db;
+        return s;
+    }
+    bool ok = true;
+    if ((s = check_finite_dev(src + hoff[0] * d, (npts - hoff[0]) * d, (int *)db->ws.ctrl.p, st, &ok))) {
+        delete db;
+        return s;
+    }
+    if (!ok) {
+        delete db;
+        return set_error(KNN_ERR_INVALID, "database contains NaN or Inf");
+    }
+    launch_repack(src, (const int64_t *)off_stage.p, (const int *)db->id.p, N, d, deff,
+                  (const int64_t *)db->off.p, (float *)db->data.p, st);
+    e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        delete db;
+        return cuda_error(e, "repack database");
+    }
+    *out = db;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_db_destroy(knn_db *db)
+{
+    if (!db)
+        return set_error(KNN_ERR_INVALID, "db is NULL");
+    cudaDeviceSynchronize();
+    delete db;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_db_info(const knn_db *db, int64_t *n_series, int32_t *d,
+                                  int32_t *n_buckets)
+{
+    if (!db)
+        return set_error(KNN_ERR_INVALID, "db is NULL");
+    if (n_series)
+        *n_series = db->N;
+    if (d)
+        *d = db->d;
+    if (n_buckets)
+        *n_buckets = (int32_t)db->buckets.size();
+    return KNN_OK;
+}

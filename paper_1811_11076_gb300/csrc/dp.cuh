@@ -1,0 +1,281 @@
+// Banded DTW / DK dynamic program over a queue of (query, series) pairs.
+//
+// Recurrences (Section 2.1; band of Section 2.2), 0-based cells (i, j) with
+// |i - j| <= r:
+//   DTW: D(i,j) = c(i,j) + min(D(i-1,j), D(i,j-1), D(i-1,j-1)),
+//        c = ||q_i - x_j||^2
+//   DK:  D(i,j) = max(c(i,j), min(...)) on squared costs; DK = sqrt(D(m-1,n-1))
+// (sqrt is monotone, so max/min commute with it exactly).
+//
+// Work mapping.  A group of G lanes owns one (query, series) pair; a warp
+// holds 32/G groups.  Lane lam of a group owns the 2P consecutive band
+// diagonals delta = j - i in [lo + 2P*lam, lo + 2P*(lam+1)), lo even and
+// <= -r, so G*P >= r+1 lanes-slots cover the band.  Cells are swept by
+// anti-diagonals t = i + j; a "step" s computes t = 2s (even diagonals) and
+// then t = 2s+1 (odd diagonals).  On one anti-diagonal every cell is
+// independent, and a cell needs only its two neighbouring diagonals from
+// t-1 (one of them possibly in the adjacent lane: one shuffle per
+// anti-diagonal) and its own diagonal from t-2.  So a lane does P
+// independent cells per anti-diagonal with no serial chain.
+//
+// The query rows and series columns a lane touches slide by one per step: a
+// ring of U = P+1 points each, refreshed by one load per step, indexed with
+// compile-time positions inside a U-times unrolled step loop.  Cells outside
+// the band get +inf through the FMA accumulator of their cost (mask 0/inf).
+//
+// Early abandoning (Section 4, first paragraph; Algorithm 3's empty active
+// set for DK): the last two anti-diagonals form a cut of every warping path,
+// and costs are non-negative, so their minimum bounds D(m-1,n-1) from below.
+// Every U steps the group compares that minimum with the live threshold of
+// its query and gives up if it is exceeded.  For DK this is the sparse DK of
+// Algorithm 3: a cell above the threshold can never lead to a result below
+// it, so the pair is dropped as soon as no cell of the cut is below.
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace knn {
+
+constexpr int DP_THREADS = 128;
+
+template <int D, int P, int KIND>
+__global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
+{
+    constexpr int U = P + 1;
+    const int lane = threadIdx.x & 31;
+    const int G = a.G;
+    const int lam = lane & (G - 1);
+    const int gbase = lane & ~(G - 1);
+    const unsigned lt_mask = (1u << gbase) - 1u;
+
+    float qw[U][D], xw[U][D];
+    float E[P], O[P], mE[P], mO[P];
+#pragma unroll
+    for (int e = 0; e < P; ++e) {
+        E[e] = O[e] = KNN_INF;
+        mE[e] = mO[e] = KNN_INF;
+    }
+#pragma unroll
+    for (int p = 0; p < U; ++p)
+#pragma unroll
+        for (int k = 0; k < D; ++k) qw[p][k] = xw[p][k] = 0.f;
+
+    const float *qp = a.q;
+    const float *xp = a.db;
+    int m = 1, n = 1, h = 0, r = 0;
+    int s_f = -1, fin_lane = 0, fin_slot = 0, fin_odd = 0;
+    int qi = 0, ci = 0, cur_idx = 0;
+    bool active = false, done = false;
+    float result = KNN_INF;
+    int s0 = 0;
+
+    int wbase = 0, wcur = 32;
+    const int n_items = (int)min((int64_t)*a.n_items, a.items_cap);
+
+    unsigned long long st_calls = 0, st_aband = 0, st_cells = 0, st_pruned = 0;
+
+    for (;;) {
+        // ---- hand out work to groups that need it (warp-converged) ---------
+        for (;;) {
+            const bool need = !active && !done;
+            const unsigned needy = __ballot_sync(KNN_FULL_MASK, need && lam == 0);
+            if (needy == 0)
+                break;
+            if (wcur >= 32) {
+                int b = 0;
+                if (lane == 0)
+                    b = atomicAdd(a.head, 32);
+                wbase = __shfl_sync(KNN_FULL_MASK, b, 0);
+                wcur = 0;
+            }
+            const int avail = 32 - wcur;
+            const int rank = __popc(needy & lt_mask);
+            const int served = min(__popc(needy), avail);
+            if (need && rank < avail) {
+                const int idx = wbase + wcur + rank;
+                if (idx >= n_items) {
+                    done = true;
+                } else {
+                    const int2 it = a.items[idx];
+                    const float lb = a.item_lb[idx];
+                    const float thr = a.out_pair ? KNN_INF : ld_volatile_f32(a.thr + it.y);
+                    const int mm = a.q_len[it.y], nn = a.db_len[it.x];
+                    if (abs(mm - nn) > band_radius(mm, nn, a.band)) {
+                        // end cell outside the band: distance +inf, nothing to run
+                        if (a.out_pair && lam == 0)
+                            a.out_pair[idx] = KNN_INF;
+                    } else if (lb > thr * a.mu_prune) {
+                        st_pruned += (lam == 0);
+                    } else {
+                        ci = it.x;
+                        qi = it.y;
+                        cur_idx = idx;
+                        m = a.q_len[qi];
+                        qp = a.q + a.q_off[qi];
+                        n = a.db_len[ci];
+                        xp = a.db + a.db_off[ci];
+                        r = band_radius(m, n, a.band);
+                        const int lo = -(r + (r & 1));
+                        h = lo / 2 + P * lam;
+#pragma unroll
+                        for (int e = 0; e < P; ++e) {
+                            const int de = lo + 2 * P * lam + 2 * e;
+                            mE[e] = (abs(de) <= r) ? 0.f : KNN_INF;
+                            mO[e] = (abs(de + 1) <= r) ? 0.f : KNN_INF;
+                            E[e] = (de == 0) ? 0.f : KNN_INF;
+                            O[e] = KNN_INF;
+                        }
+                        const int off = (n - m) - lo;
+                        fin_lane = off / (2 * P);
+                        fin_slot = (off % (2 * P)) >> 1;
+                        fin_odd = off & 1;
+                        s_f = (m + n - 2) >> 1;
+#pragma unroll
+                        for (int p = 0; p < U; ++p) {
+                            const int row = -h - ((U - p) % U);
+                            load_point<D>(qp + clampi(row, 0, m - 1) * D, qw[p]);
+                            load_point<D>(xp + clampi(h + p, 0, n - 1) * D, xw[p]);
+                        }
+                        s0 = 0;
+                        result = KNN_INF;
+                        active = true;
+                        st_calls += (lam == 0);
+                    }
+                }
+            }
+            wcur += served;
+        }
+        if (__all_sync(KNN_FULL_MASK, done))
+            break;
+
+        // ---- U steps of the wavefront ----------------------------------------
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int s = s0 + u;
+            load_point<D>(qp + clampi(s - h, 0, m - 1) * D, qw[u]);
+            load_point<D>(xp + clampi(s + h + P, 0, n - 1) * D, xw[(u + P) % U]);
+
+            float up = __shfl_up_sync(KNN_FULL_MASK, O[P - 1], 1, G);
+            up = (lam == 0) ? KNN_INF : up;
+#pragma unroll
+            for (int e = 0; e < P; ++e) {
+                const float c = sqdist_acc<D>(qw[((u - e) % U + U) % U], xw[(u + e) % U], mE[e]);
+                const float left = (e == 0) ? up : O[e - 1];
+                const float mn = fminf(fminf(left, O[e]), E[e]);
+                E[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
+            }
+            float dn = __shfl_down_sync(KNN_FULL_MASK, E[0], 1, G);
+            dn = (lam == G - 1) ? KNN_INF : dn;
+#pragma unroll
+            for (int e = 0; e < P; ++e) {
+                const float c =
+                    sqdist_acc<D>(qw[((u - e) % U + U) % U], xw[(u + e + 1) % U], mO[e]);
+                const float right = (e == P - 1) ? dn : E[e + 1];
+                const float mn = fminf(fminf(E[e], right), O[e]);
+                O[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
+            }
+            if (s == s_f && lam == fin_lane) {
+                float v = KNN_INF;
+#pragma unroll
+                for (int e = 0; e < P; ++e)
+                    if (e == fin_slot)
+                        v = fin_odd ? O[e] : E[e];
+                result = v;
+            }
+        }
+        s0 += U;
+
+        // ---- finish or abandon (group-wide) ------------------------------------
+        const float res = __shfl_sync(KNN_FULL_MASK, result, gbase + fin_lane);
+        float mn = KNN_INF;
+#pragma unroll
+        for (int e = 0; e < P; ++e)
+            mn = fminf(mn, fminf(E[e], O[e]));
+        for (int o = 1; o < G; o <<= 1)
+            mn = fminf(mn, __shfl_xor_sync(KNN_FULL_MASK, mn, o));
+        if (active) {
+            const float thr = a.out_pair ? KNN_INF : ld_volatile_f32(a.thr + qi);
+            const float lim = thr * a.mu_keep;
+            const bool finished = (s0 - 1 >= s_f);
+            if (finished) {
+                if (lam == 0) {
+                    // exact band cells of the m x n matrix
+                    long long cells = 0;
+                    for (int dlt = -r; dlt <= r; ++dlt) {
+                        const int hi = min(m, n - dlt), loi = max(0, -dlt);
+                        cells += max(0, hi - loi);
+                    }
+                    st_cells += cells;
+                    if (a.out_pair) {
+                        a.out_pair[cur_idx] = res;
+                    } else if (res <= lim && res < KNN_INF) {
+                        const unsigned long long key = make_key(res, (uint32_t)a.db_id[ci]);
+                        if (a.k > 0) {
+                            unsigned long long *sl = a.slots + (size_t)qi * a.kslots;
+                            topk_insert(sl, a.kslots, key);
+                            const unsigned long long kth = ld_volatile_u64(sl + a.k - 1);
+                            if (kth != KNN_EMPTY_KEY)
+                                atomic_min_pos_float(a.thr + qi, key_dist(kth));
+                        } else {
+                            const int pos = atomicAdd(a.eps_count + qi, 1);
+                            if (pos < a.eps_cap)
+                                a.eps_list[(size_t)qi * a.eps_cap + pos] = key;
+                        }
+                    }
+                }
+                active = false;
+            } else if (mn > lim) {
+                if (lam == 0) {
+                    st_aband += 1;
+                    long long full = 0;
+                    long long part = (long long)(2 * s0) * (2 * r + 1) / 2;
+                    for (int dlt = -r; dlt <= r; ++dlt) {
+                        const int hi = min(m, n - dlt), loi = max(0, -dlt);
+                        full += max(0, hi - loi);
+                    }
+                    st_cells += part < full ? part : full;
+                }
+                active = false;
+            }
+        }
+    }
+
+    // ---- counters: one atomic per warp per counter --------------------------
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_calls += __shfl_xor_sync(KNN_FULL_MASK, st_calls, o);
+        st_aband += __shfl_xor_sync(KNN_FULL_MASK, st_aband, o);
+        st_cells += __shfl_xor_sync(KNN_FULL_MASK, st_cells, o);
+        st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
+    }
+    if (lane == 0 && a.stats) {
+        atomicAdd(a.stats + STAT_DP_CALLS, st_calls);
+        atomicAdd(a.stats + STAT_DP_ABANDONED, st_aband);
+        atomicAdd(a.stats + STAT_DP_CELLS, st_cells);
+        atomicAdd(a.stats + STAT_LB_PRUNED_LATE, st_pruned);
+    }
+}
+
+template <int D, int P>
+bool dp_launch_tpl(const DpArgs &a, int kind, int grid, cudaStream_t st)
+{
+    if (kind == 0)
+        dp_kernel<D, P, 0><<<grid, DP_THREADS, 0, st>>>(a);
+    else
+        dp_kernel<D, P, 1><<<grid, DP_THREADS, 0, st>>>(a);
+    return true;
+}
+
+template <int D, int P>
+int dp_occupancy_tpl(int kind)
+{
+    int blocks = 0;
+    if (kind == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dp_kernel<D, P, 0>, DP_THREADS, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dp_kernel<D, P, 1>, DP_THREADS, 0);
+    return blocks;
+}
+
+}  // namespace knn

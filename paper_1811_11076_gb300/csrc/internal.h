@@ -1,0 +1,206 @@
+// Internal host-side declarations: device argument blocks and launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace knn {
+
+// Thresholds and prune margins live in "internal units": DTW as the sum of
+// squared costs, DK as the squared max cost (sqrt is monotone, so order and
+// comparisons carry over).  A bound prunes when it exceeds thr * mu_prune; a
+// finished distance is kept when it is at most thr * mu_keep.  The margins
+// cover FP32 summation drift so that no candidate of the exact FP64 answer
+// is ever dropped.
+struct Margins {
+    float mu_keep;
+    float mu_prune;
+    float rerank_rel;  // relative width of the FP64 re-scoring band
+};
+
+// -- envelope --------------------------------------------------------------
+struct EnvArgs {
+    const float *q;          // repacked queries
+    const int64_t *q_off;    // float offset of each query
+    const int *q_len;
+    int nq;
+    int d;
+    float band;
+    int n_hi;                // longest series of the bucket (envelope length)
+    int radius;              // >= 0: explicit band radius; < 0: from band
+    int64_t env_stride;      // floats between consecutive queries' lo arrays
+    float *lo;               // [nq][env_stride]
+    float *hi;
+};
+void launch_envelope(const EnvArgs &a, cudaStream_t st);
+
+// -- LB_Box stream ------------------------------------------------------------
+struct LbArgs {
+    const float *db;           // repacked database
+    const int64_t *db_off;     // float offset per (bucket-ordered) series
+    const int *db_len;
+    int c_begin, c_end;        // series range of this bucket
+    const int *q_len;
+    int q_first;               // first query of this batch
+    int nq;
+    float band;
+    const float *env_lo, *env_hi;
+    int64_t env_stride;
+    int env_floats;            // floats of one envelope (chunk padded)
+    const float *thr;          // [nq] live thresholds
+    float mu_prune;
+    const uint32_t *skip;      // [nq][words] bitmap of series already scored (nullable)
+    int skip_words;
+    int2 *items;               // out: (series, query) survivors
+    float *item_lb;            // out: their bounds
+    int *n_items;
+    int64_t capacity;
+    float *out_lb;             // optional: every bound, [nq][n_series] (component API)
+    int64_t out_lb_stride;
+    unsigned long long *stats; // [STAT_*]
+    int *status;
+};
+void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
+void lb_init_attributes();
+
+// -- greedy upper bound (Algorithm 1) ---------------------------------------
+struct GreedyArgs {
+    const float *db;
+    const int64_t *db_off;
+    const int *db_len;
+    const int *db_id;
+    int c_begin, c_end;
+    const float *q;
+    const int64_t *q_off;
+    const int *q_len;
+    int nq;
+    float band;
+    int k;
+    unsigned long long *ub_slots;  // [nq][k] smallest upper bounds (keys)
+    float *thr;                    // [nq] threshold, lowered to the k-th bound
+    float *out_ub;                 // optional: every bound [nq][stride]
+    int64_t out_stride;
+    unsigned long long *stats;
+};
+void launch_greedy(const GreedyArgs &a, int d, int form, cudaStream_t st);
+
+// -- banded dynamic program on the survivor queue ----------------------------
+struct DpArgs {
+    const int2 *items;
+    const float *item_lb;
+    const int *n_items;
+    int64_t items_cap;         // entries beyond this were never written
+    int *head;                 // queue cursor, zero before the launch
+    const float *db;
+    const int64_t *db_off;
+    const int *db_len;
+    const int *db_id;
+    const float *q;
+    const int64_t *q_off;
+    const int *q_len;
+    float band;
+    int G;                     // lanes per candidate (power of two <= 32)
+    float *thr;                // [nq] live thresholds (internal units)
+    float mu_keep, mu_prune;
+    int k;                     // > 0: k-NN
+    int kslots;                // slots kept per query (k + rerank spare)
+    unsigned long long *slots; // [nq][kslots]
+    unsigned long long *eps_list;  // eps-NN: [nq][eps_cap]
+    int *eps_count;
+    int eps_cap;
+    float *out_pair;           // pair mode: result per queue entry, no threshold
+    unsigned long long *stats;
+    int *status;
+};
+// Returns false if no kernel is compiled for (d, P).
+bool launch_dp(const DpArgs &a, int d, int P, int kind, int grid, cudaStream_t st);
+int dp_block_threads();
+// Largest P compiled for this d, and the list of compiled P values.
+int dp_num_variants(int d);
+int dp_variant_P(int d, int idx);
+int dp_max_blocks_per_sm(int d, int P, int kind);
+
+// -- finalise: sort, FP64 re-scoring of the boundary band, output -----------
+struct FinArgs {
+    int nq;
+    int k;
+    int kslots;
+    unsigned long long *slots;     // k-NN: [nq][kslots], ascending
+    unsigned long long *eps_list;  // eps-NN: [nq][eps_cap] (sorted in place)
+    const int *eps_count;
+    int eps_cap;
+    int kind;
+    float band;
+    float eps_int;             // eps-NN threshold (internal units)
+    float rerank_rel;
+    int sort_cap;              // power of two >= every per-query list
+    int *fin_valid;            // [nq] scratch
+    double *fin_vals;          // [nq][fin_width] scratch
+    int fin_width;
+    int2 *rer_list;            // (query, position) of entries to re-score
+    int *rer_count;
+    int rer_cap;
+    double *rer_scratch;       // [rer_cap][2][rer_row]
+    int rer_row;               // longest band row supported (2r+1)
+    // data for FP64 re-scoring (caller ids -> database rows)
+    const float *db;
+    const int64_t *db_off_by_id;
+    const int *db_len_by_id;
+    const float *q;
+    const int64_t *q_off;
+    const int *q_len;
+    int d;
+    int64_t *out_ids;          // device
+    float *out_dist;
+    int64_t *out_counts;       // nullable
+    int out_width;
+    unsigned long long *stats;
+    int *status;
+};
+void launch_finalize(const FinArgs &a, cudaStream_t st);
+void fin_init_attributes();
+
+// -- pair programs (no pruning) ----------------------------------------------
+void launch_pairwise64(const float *a, const int64_t *a_off, const float *b, const int64_t *b_off,
+                       const int64_t *pa, const int64_t *pb, int64_t n, int d, float band,
+                       int kind, double *out, double *scratch, int row, int threads_total,
+                       cudaStream_t st);
+
+// -- small utilities ------------------------------------------------------------
+void launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st);
+void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st);
+// Copy series order[c] of `src` (d floats per point, point offsets
+// src_off) to dst + dst_off[c] with deff floats per point (extra coordinates
+// zero) and zero padding up to the chunk-padded size.
+void launch_repack(const float *src, const int64_t *src_off, const int *order, int nser, int d,
+                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st);
+// dst[q][id[c]] = src[q][c] for c < n (bucket order -> caller order).
+void launch_scatter_by_id(const float *src, const int *db_id, int n, int nq, int64_t src_stride,
+                          float *dst, int64_t dst_stride, int out_sqrt, cudaStream_t st);
+
+enum Stat : int {
+    STAT_PAIRS = 0,
+    STAT_INFEASIBLE,
+    STAT_UB_WALKS,
+    STAT_SEEDS,
+    STAT_LB_PRUNED,
+    STAT_LB_PRUNED_LATE,
+    STAT_DP_CALLS,
+    STAT_DP_ABANDONED,
+    STAT_DP_CELLS,
+    STAT_RERANKED,
+    STAT_COUNT
+};
+
+// Band radius: r = floor(band * max(m, n)), band >= 1 unconstrained.
+__host__ __device__ inline int band_radius(int m, int n, float band)
+{
+    int L = m > n ? m : n;
+    if (band >= 1.0f)
+        return L;
+    double v = static_cast<double>(band) * static_cast<double>(L);
+    int r = static_cast<int>(v);  // v >= 0: truncation is floor
+    return r;
+}
+
+}  // namespace knn

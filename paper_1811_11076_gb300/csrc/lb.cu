@@ -1,0 +1,317 @@
+// LB_Box stream (Section 3, Eq. 1) and the query envelope (Sections 2.3, 3).
+//
+// LB_Box(X, env(Q)) = sum_i sum_j (x_ij - clamp(x_ij, l_ij, u_ij))^2 over the
+// points i of a database series X, with the per-dimension band envelope
+// [l, u] of the query Q.  Banded DTW is symmetric, so putting the envelope on
+// the query (computed once per query) bounds DTW(Q, X) just as the paper's
+// envelope on the candidate does.  The max form max_i sum_j (...)^2 bounds
+// DK^2: every point of X is coupled to some query point inside its box.
+//
+// Layout: a series is stored as whole "chunks" of lcm(d, 4) floats (whole
+// points and whole float4 vectors); lane L of a warp takes chunks L, L+32,
+// ... of one series, so consecutive lanes read consecutive 16-byte vectors
+// (coalesced, vectorised), and the envelope of the query, staged once per
+// CTA into shared memory by a TMA bulk copy, is read with the same indices.
+#include "common.cuh"
+#include "internal.h"
+
+namespace knn {
+
+constexpr int LB_THREADS = 256;
+constexpr int LB_WARPS = LB_THREADS / 32;
+
+// ---------------------------------------------------------------------------
+// envelope: direct window scan, one thread per (position, coordinate)
+
+__global__ void envelope_kernel(const EnvArgs a)
+{
+    const int qb = blockIdx.y;
+    const int m = a.q_len[qb];
+    const float *q = a.q + a.q_off[qb];
+    const int r = a.radius >= 0 ? a.radius : band_radius(m, a.n_hi, a.band);
+    const int d = a.d;
+    float *lo = a.lo + (int64_t)qb * a.env_stride;
+    float *hi = a.hi + (int64_t)qb * a.env_stride;
+    const int total = (int)a.env_stride;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int i = e / d, j = e - (e / d) * d;
+        float l = KNN_INF, u = -KNN_INF;
+        if (i < a.n_hi) {
+            const int p0 = max(0, i - r), p1 = min(m - 1, i + r);
+            for (int p = p0; p <= p1; ++p) {
+                const float v = q[(int64_t)p * d + j];
+                l = fminf(l, v);
+                u = fmaxf(u, v);
+            }
+        } else {
+            l = 0.f;  // chunk padding, never read for a real point
+            u = 0.f;
+        }
+        lo[e] = l;
+        hi[e] = u;
+    }
+}
+
+void launch_envelope(const EnvArgs &a, cudaStream_t st)
+{
+    const int threads = 256;
+    int bx = (int)((a.env_stride + threads - 1) / threads);
+    bx = bx < 64 ? bx : 64;
+    dim3 grid(bx > 0 ? bx : 1, a.nq);
+    envelope_kernel<<<grid, threads, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy global -> shared, completion tracked by an mbarrier
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                             uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for phase 0 of the barrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait0(uint64_t *bar)
+{
+    for (uint32_t it = 0; it < KNN_SPIN_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(0u)
+            : "memory");
+        if (ok)
+            return true;
+        if (it > 64)
+            __nanosleep(256);
+    }
+    return false;
+}
+
+// One chunk of PPC whole points: accumulate the squared box distance of
+// each point (sum form) or its max (max form) into acc.
+template <int D, int PPC, int F4, int FORM>
+__device__ __forceinline__ void lb_chunk(const float4 (&xv)[F4], const float4 *lo_s,
+                                         const float4 *hi_s, int ch, int n, float &acc)
+{
+    float v[4 * F4], l[4 * F4], u[4 * F4];
+#pragma unroll
+    for (int f = 0; f < F4; ++f) {
+        const float4 lv = lo_s[ch * F4 + f];
+        const float4 uv = hi_s[ch * F4 + f];
+        v[4 * f] = xv[f].x; v[4 * f + 1] = xv[f].y; v[4 * f + 2] = xv[f].z; v[4 * f + 3] = xv[f].w;
+        l[4 * f] = lv.x; l[4 * f + 1] = lv.y; l[4 * f + 2] = lv.z; l[4 * f + 3] = lv.w;
+        u[4 * f] = uv.x; u[4 * f + 1] = uv.y; u[4 * f + 2] = uv.z; u[4 * f + 3] = uv.w;
+    }
+#pragma unroll
+    for (int p = 0; p < PPC; ++p) {
+        float box = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const float x = v[p * D + k];
+            const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
+            box = __fmaf_rn(e, e, box);
+        }
+        if (ch * PPC + p < n)
+            acc = FORM == 0 ? acc + box : fmaxf(acc, box);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LB_Box stream kernel: grid (x: series tiles, y: queries of the batch)
+
+template <int D, int FORM>
+__global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
+{
+    constexpr int CH = chunk_floats(D);
+    constexpr int PPC = chunk_points(D);
+    constexpr int F4 = CH / 4;
+    extern __shared__ __align__(128) float4 env_s[];  // lo chunks then hi chunks
+    __shared__ __align__(8) uint64_t bar;
+
+    const int qb = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float4 *lo_s = env_s;
+    const float4 *hi_s = env_s + a.env_floats / 4;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)a.env_floats * 4u;
+        mbar_expect_tx(&bar, 2u * bytes);
+        tma_bulk_g2s(env_s, a.env_lo + (int64_t)qb * a.env_stride, bytes, &bar);
+        tma_bulk_g2s(env_s + a.env_floats / 4, a.env_hi + (int64_t)qb * a.env_stride, bytes, &bar);
+    }
+    if (!mbar_wait0(&bar)) {
+        if (lane == 0)
+            atomicOr(a.status, KNN_DEV_TIMEOUT);
+        return;
+    }
+
+    const int m = a.q_len[qb];
+    const int nser = a.c_end - a.c_begin;
+    const int ntiles = (nser + 31) / 32;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0;
+
+    for (int t = blockIdx.x + gridDim.x * warp; t < ntiles; t += gridDim.x * LB_WARPS) {
+        const int c0 = a.c_begin + t * 32;
+        const int cnt = min(32, a.c_end - c0);
+        float my_lb = KNN_INF;
+        bool my_feasible = false;
+        for (int jj = 0; jj < cnt; ++jj) {
+            const int c = c0 + jj;
+            const int n = a.db_len[c];
+            const int r = band_radius(m, n, a.band);
+            const bool feasible = abs(m - n) <= r;
+            float acc = 0.f;
+            if (feasible) {
+                const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+                const int nch = (n + PPC - 1) / PPC;
+                // two chunks per lane per iteration: six to eight independent
+                // 16-byte loads in flight per lane before any arithmetic
+                for (int ch0 = lane; ch0 < nch; ch0 += 64) {
+                    const int ch1 = ch0 + 32;
+                    float4 xa[F4], xb[F4];
+#pragma unroll
+                    for (int f = 0; f < F4; ++f)
+                        xa[f] = __ldg(x4 + ch0 * F4 + f);
+                    if (ch1 < nch) {
+#pragma unroll
+                        for (int f = 0; f < F4; ++f)
+                            xb[f] = __ldg(x4 + ch1 * F4 + f);
+                    }
+                    lb_chunk<D, PPC, F4, FORM>(xa, lo_s, hi_s, ch0, n, acc);
+                    if (ch1 < nch)
+                        lb_chunk<D, PPC, F4, FORM>(xb, lo_s, hi_s, ch1, n, acc);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float other = __shfl_xor_sync(KNN_FULL_MASK, acc, o);
+                    acc = FORM == 0 ? acc + other : fmaxf(acc, other);
+                }
+            } else {
+                acc = KNN_INF;
+            }
+            if (lane == jj) {
+                my_lb = acc;
+                my_feasible = feasible;
+            }
+        }
+        const int c = c0 + lane;
+        const bool valid = lane < cnt;
+        bool keep = valid && my_feasible;
+        if (keep && a.skip) {
+            const int id = c;  // skip bitmap is indexed by bucket-ordered series
+            keep = !((a.skip[(int64_t)qb * a.skip_words + (id >> 5)] >> (id & 31)) & 1u);
+        }
+        const float thr = ld_volatile_f32(a.thr + qb);
+        const bool pruned = keep && !(my_lb <= thr * a.mu_prune);
+        keep = keep && !pruned;
+        if (valid && a.out_lb)
+            a.out_lb[(int64_t)qb * a.out_lb_stride + c] = my_lb;
+        st_pairs += valid;
+        st_inf += valid && !my_feasible;
+        st_pruned += pruned;
+        const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
+        if (kb && a.items) {
+            int base = 0;
+            if (lane == 0)
+                base = atomicAdd(a.n_items, __popc(kb));
+            base = __shfl_sync(KNN_FULL_MASK, base, 0);
+            if (keep) {
+                const int64_t pos = (int64_t)base + __popc(kb & ((1u << lane) - 1u));
+                if (pos < a.capacity) {
+                    a.items[pos] = make_int2(c, qb);
+                    a.item_lb[pos] = my_lb;
+                } else {
+                    atomicOr(a.status, KNN_DEV_CAPACITY);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_pairs += __shfl_xor_sync(KNN_FULL_MASK, st_pairs, o);
+        st_inf += __shfl_xor_sync(KNN_FULL_MASK, st_inf, o);
+        st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
+    }
+    if (lane == 0 && a.stats) {
+        atomicAdd(a.stats + STAT_PAIRS, st_pairs);
+        atomicAdd(a.stats + STAT_INFEASIBLE, st_inf);
+        atomicAdd(a.stats + STAT_LB_PRUNED, st_pruned);
+    }
+}
+
+template <int D>
+static void lb_attr_d()
+{
+    cudaFuncSetAttribute(lb_kernel<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(lb_kernel<D, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void lb_init_attributes()
+{
+    lb_attr_d<1>(); lb_attr_d<2>(); lb_attr_d<3>(); lb_attr_d<4>(); lb_attr_d<5>();
+    lb_attr_d<6>(); lb_attr_d<7>(); lb_attr_d<8>(); lb_attr_d<16>();
+}
+
+template <int D>
+static void lb_launch_d(const LbArgs &a, int form, int n_sm, cudaStream_t st)
+{
+    const size_t smem = (size_t)a.env_floats * 4 * 2;
+    auto kern = form == 0 ? lb_kernel<D, 0> : lb_kernel<D, 1>;
+    const int nser = a.c_end - a.c_begin;
+    const int ntiles = (nser + 31) / 32;
+    int want = (n_sm * 4 + a.nq - 1) / a.nq;
+    int maxx = (ntiles + LB_WARPS - 1) / LB_WARPS;
+    int bx = want < maxx ? want : maxx;
+    if (bx < 1)
+        bx = 1;
+    dim3 grid(bx, a.nq);
+    kern<<<grid, LB_THREADS, smem, st>>>(a);
+}
+
+void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st)
+{
+    switch (d) {
+    case 1: lb_launch_d<1>(a, form, n_sm, st); break;
+    case 2: lb_launch_d<2>(a, form, n_sm, st); break;
+    case 3: lb_launch_d<3>(a, form, n_sm, st); break;
+    case 4: lb_launch_d<4>(a, form, n_sm, st); break;
+    case 5: lb_launch_d<5>(a, form, n_sm, st); break;
+    case 6: lb_launch_d<6>(a, form, n_sm, st); break;
+    case 7: lb_launch_d<7>(a, form, n_sm, st); break;
+    case 8: lb_launch_d<8>(a, form, n_sm, st); break;
+    case 16: lb_launch_d<16>(a, form, n_sm, st); break;
+    default: break;
+    }
+}
+
+}  // namespace knn

@@ -1,0 +1,613 @@
+// knn_scan: batch planning and the launch sequence of the exact scan.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "runtime.h"
+
+using namespace knn;
+
+namespace {
+
+struct Segment {
+    int b_begin, b_end;  // buckets [b_begin, b_end)
+    int P, G;
+    int64_t base, cap;   // region of the survivor queue
+};
+
+struct Plan {
+    int nq = 0;
+    std::vector<int> m;
+    std::vector<int64_t> qoff;  // float offsets of the repacked queries
+    int64_t qfloats = 0;
+    int max_m = 0;
+    int64_t env_stride = 0;
+    std::vector<Segment> segs;
+    std::vector<int> seg_of_bucket;
+    int64_t items_cap = 0;
+    int k = 0, kslots = 0, width = 0, sort_cap = 0;
+    int64_t eps_cap = 0;
+    Margins mg{};
+    float eps_int = 0.f;
+    int rer_row = 0, rer_cap = 0;
+};
+
+knn_status grow(Workspace &ws, DevBuf &b, size_t bytes)
+{
+    if (bytes <= b.bytes)
+        return KNN_OK;
+    ws.generation++;
+    return b.ensure(bytes < 256 ? 256 : bytes);
+}
+
+int next_pow2i(int v)
+{
+    int p = 1;
+    while (p < v)
+        p <<= 1;
+    return p;
+}
+
+DpChoice dp_choice(knn_db *db, int kind, int r, int n)
+{
+    auto it = db->tuned.find(std::make_tuple(kind, r, n));
+    if (it != db->tuned.end())
+        return it->second;
+    DpChoice c;
+    choose_dp_config(db->deff, r, n, &c.P, &c.G);
+    return c;
+}
+
+knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int nq,
+                     const knn_params &p, Plan &pl)
+{
+    const int CH = chunk_floats(db->deff), PPC = chunk_points(db->deff);
+    pl.nq = nq;
+    pl.m.resize(nq);
+    pl.qoff.resize(nq);
+    pl.qfloats = 0;
+    pl.max_m = 0;
+    for (int i = 0; i < nq; ++i) {
+        const int m = (int)(hq_off[q0 + i + 1] - hq_off[q0 + i]);
+        pl.m[i] = m;
+        pl.qoff[i] = pl.qfloats;
+        pl.qfloats += (int64_t)((m + PPC - 1) / PPC) * CH;
+        pl.max_m = std::max(pl.max_m, m);
+    }
+    pl.env_stride = 0;
+    for (auto &b : db->buckets)
+        pl.env_stride = std::max<int64_t>(pl.env_stride, (int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
+    if (pl.env_stride * 2 * 4 > 200 * 1024)
+        return set_error(KNN_ERR_UNSUPPORTED, "envelope larger than shared memory (length x d)");
+
+    // DP segments: consecutive buckets sharing a (P, G) choice
+    pl.segs.clear();
+    pl.seg_of_bucket.assign(db->buckets.size(), 0);
+    int64_t base = 0;
+    for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
+        const Bucket &b = db->buckets[bi];
+        const int r = band_radius(pl.max_m, b.n_hi, p.band);
+        DpChoice c = dp_choice(db, p.distance, r, b.n_hi);
+        if (c.P == 0)
+            return set_error(KNN_ERR_UNSUPPORTED, "band too wide for the compiled DP variants");
+        const int64_t cap = (int64_t)nq * (b.c_end - b.c_begin);
+        if (!pl.segs.empty() && pl.segs.back().P == c.P && pl.segs.back().G == c.G) {
+            pl.segs.back().b_end = (int)bi + 1;
+            pl.segs.back().cap += cap;
+        } else if ((int)pl.segs.size() == MAX_SEG) {
+            // out of segments: widen the last one to cover this band too
+            Segment &s = pl.segs.back();
+            s.b_end = (int)bi + 1;
+            s.cap += cap;
+            if (c.G * c.P > s.G * s.P) {
+                s.P = c.P;
+                s.G = c.G;
+            }
+        } else {
+            Segment s;
+            s.b_begin = (int)bi;
+            s.b_end = (int)bi + 1;
+            s.P = c.P;
+            s.G = c.G;
+            s.base = 0;
+            s.cap = cap;
+            pl.segs.push_back(s);
+        }
+        pl.seg_of_bucket[bi] = (int)pl.segs.size() - 1;
+    }
+    for (auto &s : pl.segs) {
+        s.base = base;
+        base += s.cap;
+    }
+    pl.items_cap = base;
+
+    pl.k = p.k;
+    pl.eps_cap = p.k > 0 ? 0 : p.eps_capacity;
+    pl.kslots = p.k > 0 ? p.k + std::max(8, p.k / 2) : 0;
+    pl.width = p.k > 0 ? p.k : (int)p.eps_capacity;
+    pl.sort_cap = next_pow2i(std::max(pl.kslots, (int)pl.eps_cap));
+    if (pl.sort_cap > 8192)
+        return set_error(KNN_ERR_UNSUPPORTED, "eps_capacity above 8192");
+    pl.mg = margins_for(p.distance, pl.max_m + db->max_len, db->deff);
+    pl.eps_int = p.distance == KNN_DK ? p.eps * p.eps : p.eps;
+    pl.rer_row = 2 * band_radius(pl.max_m, db->max_len, p.band) + 1;
+    pl.rer_cap = 1024 + 8 * nq;
+    return KNN_OK;
+}
+
+knn_status size_workspace(knn_db *db, const Plan &pl)
+{
+    Workspace &ws = db->ws;
+    const int nq = pl.nq;
+    knn_status s;
+#define G_(buf, bytes)                            \
+    if ((s = grow(ws, ws.buf, (size_t)(bytes)))) \
+        return s;
+    G_(qbuf, sizeof(float) * pl.qfloats);
+    G_(q_off, sizeof(int64_t) * nq);
+    G_(q_len, sizeof(int) * nq);
+    G_(env_lo, sizeof(float) * nq * pl.env_stride);
+    G_(env_hi, sizeof(float) * nq * pl.env_stride);
+    G_(thr, sizeof(float) * nq);
+    G_(slots, sizeof(unsigned long long) * nq * std::max(pl.kslots, 1));
+    G_(ub_slots, sizeof(unsigned long long) * nq * std::max(pl.k, 1));
+    G_(items, sizeof(int2) * pl.items_cap);
+    G_(item_lb, sizeof(float) * pl.items_cap);
+    G_(eps_list, sizeof(unsigned long long) * nq * std::max<int64_t>(pl.eps_cap, 1));
+    G_(eps_count, sizeof(int) * nq);
+    G_(ctrl, sizeof(Ctrl));
+    G_(fin_valid, sizeof(int) * nq);
+    G_(fin_vals, sizeof(double) * nq * std::max<int64_t>(pl.kslots, pl.eps_cap));
+    G_(rer_list, sizeof(int2) * pl.rer_cap);
+    G_(rer_scratch, sizeof(double) * pl.rer_cap * 2 * pl.rer_row);
+    G_(out_ids, sizeof(int64_t) * nq * pl.width);
+    G_(out_dist, sizeof(float) * nq * pl.width);
+    G_(out_counts, sizeof(int64_t) * nq);
+#undef G_
+    return KNN_OK;
+}
+
+// Optional stage events: [0] start, [1] after seeding, [2] after LB, [3] after
+// DP, [4] after finalise.
+struct StageEvents {
+    cudaEvent_t ev[5];
+};
+
+// All launches of one batch; capturable (no host synchronisation, no
+// pageable copies).  Outputs go to the given device pointers.  Returns the
+// number of kernels launched.
+int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *q_src,
+                  const int64_t *q_src_off, int64_t *o_ids, float *o_dist, int64_t *o_counts,
+                  cudaStream_t st, StageEvents *sev = nullptr)
+{
+    int launches = 0;
+    if (sev)
+        cudaEventRecord(sev->ev[0], st);
+    Workspace &ws = db->ws;
+    Ctrl *ctrl = ws.ctrl.as<Ctrl>();
+    const int nq = pl.nq;
+    const int kind = p.distance;
+    unsigned long long *stats = ctrl->stats;
+
+    launch_repack(q_src, q_src_off, nullptr, nq, db->d, db->deff, ws.q_off.as<int64_t>(),
+                  ws.qbuf.as<float>(), st);
+    cudaMemsetAsync(&ctrl->rer_count, 0, offsetof(Ctrl, stats) - offsetof(Ctrl, rer_count), st);
+    launch_fill_f32(ws.thr.as<float>(), p.k > 0 ? KNN_INF_HOST : pl.eps_int, nq, st);
+    launches += 2;
+    if (p.k > 0) {
+        launch_fill_u64(ws.slots.as<unsigned long long>(), KNN_EMPTY_KEY, (int64_t)nq * pl.kslots,
+                        st);
+        launch_fill_u64(ws.ub_slots.as<unsigned long long>(), KNN_EMPTY_KEY, (int64_t)nq * pl.k,
+                        st);
+        launches += 2;
+    } else {
+        cudaMemsetAsync(ws.eps_count.p, 0, sizeof(int) * nq, st);
+    }
+
+    // Section 4.3: upper-bound pre-pass seeds the threshold
+    if (p.k > 0 && p.seed_mode == KNN_SEED_GREEDY) {
+        for (auto &b : db->buckets) {
+            GreedyArgs g{};
+            g.db = db->data.as<float>();
+            g.db_off = db->off.as<int64_t>();
+            g.db_len = db->len.as<int>();
+            g.db_id = db->id.as<int>();
+            g.c_begin = b.c_begin;
+            g.c_end = b.c_end;
+            g.q = ws.qbuf.as<float>();
+            g.q_off = ws.q_off.as<int64_t>();
+            g.q_len = ws.q_len.as<int>();
+            g.nq = nq;
+            g.band = p.band;
+            g.k = p.k;
+            g.ub_slots = ws.ub_slots.as<unsigned long long>();
+            g.thr = ws.thr.as<float>();
+            g.stats = stats;
+            launch_greedy(g, db->deff, kind == KNN_DK ? 0 : 1, st);
+            ++launches;
+        }
+    }
+    if (sev)
+        cudaEventRecord(sev->ev[1], st);
+
+    // envelope + LB_Box stream per bucket
+    for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
+        const Bucket &b = db->buckets[bi];
+        const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];
+        const int PPC = chunk_points(db->deff), CH = chunk_floats(db->deff);
+        EnvArgs e{};
+        e.q = ws.qbuf.as<float>();
+        e.q_off = ws.q_off.as<int64_t>();
+        e.q_len = ws.q_len.as<int>();
+        e.nq = nq;
+        e.d = db->deff;
+        e.band = p.band;
+        e.n_hi = b.n_hi;
+        e.radius = -1;
+        e.env_stride = pl.env_stride;
+        e.lo = ws.env_lo.as<float>();
+        e.hi = ws.env_hi.as<float>();
+        launch_envelope(e, st);
+        LbArgs l{};
+        l.db = db->data.as<float>();
+        l.db_off = db->off.as<int64_t>();
+        l.db_len = db->len.as<int>();
+        l.c_begin = b.c_begin;
+        l.c_end = b.c_end;
+        l.q_len = ws.q_len.as<int>();
+        l.nq = nq;
+        l.band = p.band;
+        l.env_lo = ws.env_lo.as<float>();
+        l.env_hi = ws.env_hi.as<float>();
+        l.env_stride = pl.env_stride;
+        l.env_floats = (int)((int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
+        l.thr = ws.thr.as<float>();
+        l.mu_prune = pl.mg.mu_prune;
+        l.items = ws.items.as<int2>() + sg.base;
+        l.item_lb = ws.item_lb.as<float>() + sg.base;
+        l.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];
+        l.capacity = sg.cap;
+        l.stats = stats;
+        l.status = &ctrl->status;
+        launch_lb(l, db->deff, kind, db->n_sm, st);
+        launches += 2;
+    }
+    if (sev)
+        cudaEventRecord(sev->ev[2], st);
+
+    // banded DP over each segment's survivors
+    for (size_t si = 0; si < pl.segs.size(); ++si) {
+        const Segment &sg = pl.segs[si];
+        DpArgs a{};
+        a.items = ws.items.as<int2>() + sg.base;
+        a.item_lb = ws.item_lb.as<float>() + sg.base;
+        a.n_items = &ctrl->seg_count[si];
+        a.items_cap = sg.cap;
+        a.head = &ctrl->seg_head[si];
+        a.db = db->data.as<float>();
+        a.db_off = db->off.as<int64_t>();
+        a.db_len = db->len.as<int>();
+        a.db_id = db->id.as<int>();
+        a.q = ws.qbuf.as<float>();
+        a.q_off = ws.q_off.as<int64_t>();
+        a.q_len = ws.q_len.as<int>();
+        a.band = p.band;
+        a.G = sg.G;
+        a.thr = ws.thr.as<float>();
+        a.mu_keep = pl.mg.mu_keep;
+        a.mu_prune = pl.mg.mu_prune;
+        a.k = p.k;
+        a.kslots = pl.kslots;
+        a.slots = ws.slots.as<unsigned long long>();
+        a.eps_list = ws.eps_list.as<unsigned long long>();
+        a.eps_count = ws.eps_count.as<int>();
+        a.eps_cap = (int)pl.eps_cap;
+        a.stats = stats;
+        a.status = &ctrl->status;
+        const int occ = dp_max_blocks_per_sm(db->deff, sg.P, kind);
+        launch_dp(a, db->deff, sg.P, kind, db->n_sm * std::max(occ, 1), st);
+        ++launches;
+    }
+    if (sev)
+        cudaEventRecord(sev->ev[3], st);
+
+    FinArgs f{};
+    f.nq = nq;
+    f.k = p.k;
+    f.kslots = pl.kslots;
+    f.slots = ws.slots.as<unsigned long long>();
+    f.eps_list = ws.eps_list.as<unsigned long long>();
+    f.eps_count = ws.eps_count.as<int>();
+    f.eps_cap = (int)pl.eps_cap;
+    f.kind = kind;
+    f.band = p.band;
+    f.eps_int = pl.eps_int;
+    f.rerank_rel = pl.mg.rerank_rel;
+    f.sort_cap = pl.sort_cap;
+    f.fin_valid = ws.fin_valid.as<int>();
+    f.fin_vals = ws.fin_vals.as<double>();
+    f.fin_width = std::max<int>(pl.kslots, (int)pl.eps_cap);
+    f.rer_list = ws.rer_list.as<int2>();
+    f.rer_count = &ctrl->rer_count;
+    f.rer_cap = pl.rer_cap;
+    f.rer_scratch = ws.rer_scratch.as<double>();
+    f.rer_row = pl.rer_row;
+    f.db = db->data.as<float>();
+    f.db_off_by_id = db->off_by_id.as<int64_t>();
+    f.db_len_by_id = db->len_by_id.as<int>();
+    f.q = ws.qbuf.as<float>();
+    f.q_off = ws.q_off.as<int64_t>();
+    f.q_len = ws.q_len.as<int>();
+    f.d = db->deff;
+    f.out_ids = o_ids;
+    f.out_dist = o_dist;
+    f.out_counts = o_counts;
+    f.out_width = pl.width;
+    f.stats = stats;
+    f.status = &ctrl->status;
+    launch_finalize(f, st);
+    launches += 3;
+    if (sev)
+        cudaEventRecord(sev->ev[4], st);
+    return launches;
+}
+
+std::map<GraphKey, int> graph_launches;
+
+uint64_t hash_lengths(const std::vector<int> &m)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (int v : m) {
+        h ^= (uint64_t)v;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *q_offsets,
+                               int32_t n_queries, const knn_params *params, int64_t *out_ids,
+                               float *out_dist, int64_t *out_counts, knn_stats *stats,
+                               void *stream)
+{
+    if (!db || !queries || !q_offsets || !params || !out_ids || !out_dist)
+        return set_error(KNN_ERR_INVALID, "NULL argument");
+    const knn_params p = *params;
+    if (n_queries < 1)
+        return set_error(KNN_ERR_INVALID, "n_queries must be >= 1");
+    if (p.k < 0)
+        return set_error(KNN_ERR_INVALID, "k must be >= 0");
+    if (p.k > db->N)
+        return set_error(KNN_ERR_INVALID, "k larger than the number of series");
+    if (p.k > 1024)
+        return set_error(KNN_ERR_UNSUPPORTED, "k above 1024");
+    if (!(p.band > 0.f) || !std::isfinite(p.band))
+        return set_error(KNN_ERR_INVALID, "band must be a positive finite number");
+    if (p.distance != KNN_DTW && p.distance != KNN_DK)
+        return set_error(KNN_ERR_INVALID, "unknown distance");
+    if (p.k == 0) {
+        if (!(p.eps >= 0.f) || !std::isfinite(p.eps))
+            return set_error(KNN_ERR_INVALID, "eps must be finite and >= 0");
+        if (p.eps_capacity < 1)
+            return set_error(KNN_ERR_INVALID, "eps_capacity must be >= 1");
+        if (!out_counts)
+            return set_error(KNN_ERR_INVALID, "eps-NN needs out_counts");
+    }
+    if (p.seed_mode < KNN_SEED_GREEDY || p.seed_mode > KNN_SEED_NONE)
+        return set_error(KNN_ERR_INVALID, "unknown seed_mode");
+    if (p.seed_mode == KNN_SEED_LEARNED && !db->enc)
+        return set_error(KNN_ERR_INVALID, "learned seeding needs an attached encoder");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaSetDevice(db->dev);
+
+    // query offsets on the host
+    std::vector<int64_t> hq(n_queries + 1);
+    if (is_device_ptr(q_offsets)) {
+        cudaError_t e = cudaMemcpy(hq.data(), q_offsets, sizeof(int64_t) * (n_queries + 1),
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return cuda_error(e, "copy q_offsets");
+    } else {
+        memcpy(hq.data(), q_offsets, sizeof(int64_t) * (n_queries + 1));
+    }
+    if (hq[0] < 0)
+        return set_error(KNN_ERR_INVALID, "q_offsets[0] < 0");
+    for (int i = 0; i < n_queries; ++i) {
+        const int64_t L = hq[i + 1] - hq[i];
+        if (L < 1)
+            return set_error(KNN_ERR_INVALID, "query " + std::to_string(i) + " has length < 1");
+        if (L > 65536)
+            return set_error(KNN_ERR_UNSUPPORTED, "query longer than 65536 points");
+    }
+
+    Workspace &ws = db->ws;
+    knn_status s;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, st);
+
+    // queries and their point offsets on the device, relative to hq[0]
+    const int64_t qpts = hq[n_queries] - hq[0];
+    const bool q_dev = is_device_ptr(queries);
+    const bool graph = p.use_graph != 0;
+    const float *q_src = queries + hq[0] * db->d;
+    if ((s = grow(ws, ws.ctrl, sizeof(Ctrl))))
+        return s;
+    if (!q_dev || graph) {
+        if ((s = grow(ws, ws.q_raw, sizeof(float) * qpts * db->d)))
+            return s;
+        cudaError_t e = cudaMemcpyAsync(ws.q_raw.p, q_src, sizeof(float) * qpts * db->d,
+                                        q_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        st);
+        if (e != cudaSuccess)
+            return cuda_error(e, "copy queries");
+        q_src = ws.q_raw.as<float>();
+    }
+    std::vector<int64_t> rel(n_queries + 1);
+    for (int i = 0; i <= n_queries; ++i)
+        rel[i] = hq[i] - hq[0];
+    if ((s = grow(ws, ws.q_src_off, sizeof(int64_t) * (n_queries + 1))))
+        return s;
+    {
+        bool ok = true;
+        cudaError_t e = cudaMemcpyAsync(ws.q_src_off.p, rel.data(),
+                                        sizeof(int64_t) * (n_queries + 1), cudaMemcpyHostToDevice,
+                                        st);
+        if (e != cudaSuccess)
+            return cuda_error(e, "copy q offsets");
+        if ((s = check_finite_dev(q_src, qpts * db->d, &ws.ctrl.as<Ctrl>()->status, st, &ok)))
+            return s;
+        if (!ok)
+            return set_error(KNN_ERR_INVALID, "queries contain NaN or Inf");
+    }
+    cudaMemsetAsync(ws.ctrl.p, 0, sizeof(Ctrl), st);
+
+    // batches bounded so that the survivor queue stays below 2^27 entries
+    int batch = p.query_batch > 0 ? p.query_batch : n_queries;
+    const int64_t max_items = (int64_t)1 << 27;
+    batch = (int)std::max<int64_t>(1, std::min<int64_t>(batch, max_items / db->N));
+    const int width = p.k > 0 ? p.k : (int)p.eps_capacity;
+    const bool out_dev = is_device_ptr(out_ids) && is_device_ptr(out_dist) &&
+                         (!out_counts || is_device_ptr(out_counts));
+
+    int64_t launches = 1;  // the finite check
+    double stage_ms[4] = {0, 0, 0, 0};
+    const bool profile = p.profile != 0 && !graph;
+    StageEvents sev;
+    if (profile)
+        for (auto &ev : sev.ev)
+            cudaEventCreate(&ev);
+    for (int q0 = 0; q0 < n_queries; q0 += batch) {
+        const int nq = std::min(batch, n_queries - q0);
+        Plan pl;
+        if ((s = make_plan(db, hq, q0, nq, p, pl)))
+            return s;
+        const uint64_t gen0 = ws.generation;
+        if ((s = size_workspace(db, pl)))
+            return s;
+        if (ws.generation != gen0) {
+            for (auto &g : db->graphs)
+                cudaGraphExecDestroy(g.second);
+            db->graphs.clear();
+        }
+        cudaError_t e = cudaMemcpyAsync(ws.q_off.p, pl.qoff.data(), sizeof(int64_t) * nq,
+                                        cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws.q_len.p, pl.m.data(), sizeof(int) * nq, cudaMemcpyHostToDevice,
+                                st);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);  // host vectors go out of scope
+        if (e != cudaSuccess)
+            return cuda_error(e, "upload batch metadata");
+        const float *qs = q_src;
+        const int64_t *qso = ws.q_src_off.as<int64_t>() + q0;
+        int64_t *oi = ws.out_ids.as<int64_t>();
+        float *od = ws.out_dist.as<float>();
+        int64_t *oc = ws.out_counts.as<int64_t>();
+        if (!graph && out_dev) {
+            oi = out_ids + (int64_t)q0 * width;
+            od = out_dist + (int64_t)q0 * width;
+            oc = out_counts ? out_counts + q0 : nullptr;
+        }
+        if (graph) {
+            GraphKey key{nq, p.k, p.distance, p.seed_mode, p.seed_count, p.band, p.eps,
+                         p.eps_capacity, hash_lengths(pl.m) ^ ((uint64_t)q0 << 40)};
+            auto it = db->graphs.find(key);
+            if (it == db->graphs.end()) {
+                cudaGraph_t gph;
+                e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess)
+                    return cuda_error(e, "begin capture");
+                graph_launches[key] = enqueue_batch(db, pl, p, qs, qso, oi, od, oc, st);
+                e = cudaStreamEndCapture(st, &gph);
+                if (e != cudaSuccess)
+                    return cuda_error(e, "end capture");
+                cudaGraphExec_t ex;
+                e = cudaGraphInstantiate(&ex, gph, 0);
+                cudaGraphDestroy(gph);
+                if (e != cudaSuccess)
+                    return cuda_error(e, "instantiate graph");
+                it = db->graphs.emplace(key, ex).first;
+            }
+            e = cudaGraphLaunch(it->second, st);
+            if (e != cudaSuccess)
+                return cuda_error(e, "graph launch");
+            launches += graph_launches[key];
+        } else {
+            launches += enqueue_batch(db, pl, p, qs, qso, oi, od, oc, st, profile ? &sev : nullptr);
+            if (profile) {
+                e = cudaEventSynchronize(sev.ev[4]);
+                if (e != cudaSuccess)
+                    return cuda_error(e, "stage events");
+                for (int i = 0; i < 4; ++i) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, sev.ev[i], sev.ev[i + 1]);
+                    stage_ms[i] += ms;
+                }
+            }
+        }
+        if (graph || !out_dev) {
+            const cudaMemcpyKind k1 = out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            e = cudaMemcpyAsync(out_ids + (int64_t)q0 * width, oi, sizeof(int64_t) * nq * width, k1,
+                                st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(out_dist + (int64_t)q0 * width, od, sizeof(float) * nq * width,
+                                    k1, st);
+            if (e == cudaSuccess && out_counts)
+                e = cudaMemcpyAsync(out_counts + q0, oc, sizeof(int64_t) * nq, k1, st);
+            if (e != cudaSuccess)
+                return cuda_error(e, "copy outputs");
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return cuda_error(e, "launch");
+    }
+    cudaEventRecord(ev1, st);
+    Ctrl hc;
+    cudaError_t e = cudaMemcpyAsync(&hc, ws.ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_error(e, "scan");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (profile)
+        for (auto &ev : sev.ev)
+            cudaEventDestroy(ev);
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->pairs = (int64_t)hc.stats[STAT_PAIRS];
+        stats->band_infeasible = (int64_t)hc.stats[STAT_INFEASIBLE];
+        stats->ub_walks = (int64_t)hc.stats[STAT_UB_WALKS];
+        stats->seeds = (int64_t)hc.stats[STAT_SEEDS];
+        stats->lb_pruned = (int64_t)hc.stats[STAT_LB_PRUNED];
+        stats->lb_pruned_late = (int64_t)hc.stats[STAT_LB_PRUNED_LATE];
+        stats->dp_calls = (int64_t)hc.stats[STAT_DP_CALLS];
+        stats->dp_abandoned = (int64_t)hc.stats[STAT_DP_ABANDONED];
+        stats->dp_cells = (int64_t)hc.stats[STAT_DP_CELLS];
+        stats->reranked = (int64_t)hc.stats[STAT_RERANKED];
+        stats->launches = launches;
+        stats->ms_total = ms;
+        stats->ms_seed = stage_ms[0];
+        stats->ms_lb = stage_ms[1];
+        stats->ms_dp = stage_ms[2];
+        stats->ms_finalize = stage_ms[3];
+    }
+    if (hc.status & KNN_DEV_TIMEOUT)
+        return set_error(KNN_ERR_TIMEOUT, "a device wait gave up");
+    if (hc.status & KNN_DEV_BAD_SHAPE)
+        return set_error(KNN_ERR_UNSUPPORTED, "a kernel received a shape it cannot handle");
+    if (hc.status & KNN_DEV_CAPACITY)
+        return set_error(KNN_ERR_CAPACITY, p.k == 0 ? "eps-NN result exceeds eps_capacity"
+                                                    : "internal capacity exceeded");
+    return KNN_OK;
+}

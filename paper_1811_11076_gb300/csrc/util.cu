@@ -1,0 +1,95 @@
+// Small device utilities: fills, repacking into the chunked layout, scatter.
+#include "common.cuh"
+#include "internal.h"
+
+namespace knn {
+
+__global__ void fill_u64_kernel(unsigned long long *p, unsigned long long v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void fill_f32_kernel(float *p, float v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+static int blocks_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 4096)
+        b = 4096;
+    return b < 1 ? 1 : (int)b;
+}
+
+void launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st)
+{
+    if (n > 0)
+        fill_u64_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, v, n);
+}
+
+void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st)
+{
+    if (n > 0)
+        fill_f32_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, v, n);
+}
+
+// One warp per series.
+__global__ void repack_kernel(const float *src, const int64_t *src_off, const int *order, int nser,
+                              int d, int deff, const int64_t *dst_off, float *dst)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int ppc = chunk_floats(deff) / deff;  // host guarantees deff is a compiled width
+    const int chf = chunk_floats(deff);
+    for (int c = warp; c < nser; c += nw) {
+        const int s = order ? order[c] : c;
+        const int64_t b = src_off[s];
+        const int n = (int)(src_off[s + 1] - b);
+        const int64_t total = (int64_t)((n + ppc - 1) / ppc) * chf;
+        const float *sp = src + b * d;
+        float *dp = dst + dst_off[c];
+        for (int64_t f = lane; f < total; f += 32) {
+            const int64_t i = f / deff;
+            const int j = (int)(f - i * deff);
+            dp[f] = (i < n && j < d) ? sp[i * d + j] : 0.f;
+        }
+    }
+}
+
+void launch_repack(const float *src, const int64_t *src_off, const int *order, int nser, int d,
+                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st)
+{
+    if (nser <= 0)
+        return;
+    int blocks = (nser + 7) / 8;
+    if (blocks > 8192)
+        blocks = 8192;
+    repack_kernel<<<blocks, 256, 0, st>>>(src, src_off, order, nser, d, deff, dst_off, dst);
+}
+
+__global__ void scatter_kernel(const float *src, const int *db_id, int n, int64_t src_stride,
+                               float *dst, int64_t dst_stride, int out_sqrt)
+{
+    const int q = blockIdx.y;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        float v = src[(int64_t)q * src_stride + c];
+        if (out_sqrt)
+            v = sqrtf(v);
+        dst[(int64_t)q * dst_stride + db_id[c]] = v;
+    }
+}
+
+void launch_scatter_by_id(const float *src, const int *db_id, int n, int nq, int64_t src_stride,
+                          float *dst, int64_t dst_stride, int out_sqrt, cudaStream_t st)
+{
+    dim3 grid(blocks_for(n, 256) > 1024 ? 1024 : blocks_for(n, 256), nq);
+    scatter_kernel<<<grid, 256, 0, st>>>(src, db_id, n, src_stride, dst, dst_stride, out_sqrt);
+}
+
+}  // namespace knn
