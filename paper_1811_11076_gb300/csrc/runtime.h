@@ -100,10 +100,13 @@ struct knn_db {
     knn_encoder *enc = nullptr;
     knn::DevBuf emb;                      // [N][64] bf16 embeddings (caller id order)
     std::map<knn::GraphKey, cudaGraphExec_t> graphs;
+    cudaStream_t cap_stream = nullptr;    // private stream used only to capture graphs
     std::map<std::tuple<int, int, int>, knn::DpChoice> tuned;  // (kind, r, n) -> config
     ~knn_db()
     {
         for (auto &g : graphs)
             cudaGraphExecDestroy(g.second);
+        if (cap_stream)
+            cudaStreamDestroy(cap_stream);
     }
 };

@@ -521,12 +521,20 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
                          p.eps_capacity, hash_lengths(pl.m) ^ ((uint64_t)q0 << 40)};
             auto it = db->graphs.find(key);
             if (it == db->graphs.end()) {
+                // capture on a private stream (the caller's may be the legacy
+                // default stream, which cannot be captured); replay on the caller's
+                if (!db->cap_stream) {
+                    e = cudaStreamCreateWithFlags(&db->cap_stream, cudaStreamNonBlocking);
+                    if (e != cudaSuccess)
+                        return cuda_error(e, "create capture stream");
+                }
                 cudaGraph_t gph;
-                e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+                e = cudaStreamBeginCapture(db->cap_stream, cudaStreamCaptureModeThreadLocal);
                 if (e != cudaSuccess)
                     return cuda_error(e, "begin capture");
-                graph_launches[key] = enqueue_batch(db, pl, p, qs, qso, oi, od, oc, st);
-                e = cudaStreamEndCapture(st, &gph);
+                graph_launches[key] =
+                    enqueue_batch(db, pl, p, qs, qso, oi, od, oc, db->cap_stream);
+                e = cudaStreamEndCapture(db->cap_stream, &gph);
                 if (e != cudaSuccess)
                     return cuda_error(e, "end capture");
                 cudaGraphExec_t ex;
