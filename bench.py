@@ -37,6 +37,9 @@ N_SERIES, LENGTH, D, N_QUERIES = 100_000, 256, 3, 1000
 K, BAND = 10, 0.1
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+SEED_DESC = {"greedy": "greedy upper-bound pre-pass over every series (Section 4.3)",
+             "lb": "LB_Box-ordered proposals scored exactly first, then filter",
+             "none": "no seeding"}
 
 
 def peaks():
@@ -175,20 +178,22 @@ def run_gpu(args):
     kw.lib()
 
     w = workload(world)
-    q0, q1 = w.q_off[rank * N_QUERIES], w.q_off[(rank + 1) * N_QUERIES]
+    nq = args.queries
+    q0, q1 = w.q_off[rank * N_QUERIES], w.q_off[rank * N_QUERIES + nq]
     q_host = np.ascontiguousarray(w.q[q0:q1])
-    q_off = w.q_off[rank * N_QUERIES:(rank + 1) * N_QUERIES + 1] - q0
+    q_off = w.q_off[rank * N_QUERIES:rank * N_QUERIES + nq + 1] - q0
     db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
     q_dev = torch.from_numpy(q_host).cuda()
     q_off_t = torch.from_numpy(q_off)
-    ids = torch.empty((N_QUERIES, K), dtype=torch.int64, device="cuda")
-    dst = torch.empty((N_QUERIES, K), dtype=torch.float32, device="cuda")
-    cnt = torch.empty(N_QUERIES, dtype=torch.int64, device="cuda")
-    kinds = (kw.DTW, kw.DK)
+    ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
+    dst = torch.empty((nq, K), dtype=torch.float32, device="cuda")
+    cnt = torch.empty(nq, dtype=torch.int64, device="cuda")
+    kinds = {"both": (kw.DTW, kw.DK), "dtw": (kw.DTW,), "dk": (kw.DK,)}[args.only]
+    seed_mode = {"greedy": kw.SEED_GREEDY, "lb": kw.SEED_LB, "none": kw.SEED_NONE}[args.seed]
 
     def step(collect=None):
         for kind in kinds:
-            _, _, st = db.scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=kw.SEED_GREEDY,
+            _, _, st = db.scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
                                out=(ids, dst, cnt), stats=True, profile=True)
             if collect is not None:
                 collect.append((kind, st))
@@ -197,6 +202,17 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+
+    # autotuner (set-up, outside the timed region): DP shape per distance
+    shapes = {}
+    r = int(np.float64(np.float32(BAND)) * LENGTH)
+    for kind in kinds:
+        if not args.no_autotune:
+            nt = min(nq, 128)
+            db.autotune(q_dev[: int(q_off[nt])], q_off_t[: nt + 1], k=K, band=BAND, distance=kind,
+                        seed=seed_mode)
+        shapes["DTW" if kind == kw.DTW else "DK"] = dict(zip(("P", "G"),
+                                                             db.get_dp_shape(kind, r, LENGTH)))
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -215,7 +231,7 @@ def run_gpu(args):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    total_queries = N_QUERIES * len(kinds) * args.steps * world
+    total_queries = nq * len(kinds) * args.steps * world
     value = total_queries / (ms / 1000.0)
 
     # per-distance detail (this rank)
@@ -225,15 +241,16 @@ def run_gpu(args):
         agg = {key: sum(s[key] for s in sts) for key in sts[0]}
         name = "DTW" if kind == kw.DTW else "DK"
         detail[name] = {
-            "queries_per_s": N_QUERIES * len(sts) / (agg["ms_total"] / 1000.0),
+            "queries_per_s": nq * len(sts) / (agg["ms_total"] / 1000.0),
             "dp_gcups": agg["dp_cells"] / (agg["ms_dp"] / 1000.0) / 1e9 if agg["ms_dp"] else None,
             "ms_per_scan": agg["ms_total"] / len(sts),
             "ms_seed": agg["ms_seed"] / len(sts), "ms_lb": agg["ms_lb"] / len(sts),
             "ms_dp": agg["ms_dp"] / len(sts), "ms_finalize": agg["ms_finalize"] / len(sts),
-            "dp_calls_per_query": agg["dp_calls"] / (N_QUERIES * len(sts)),
+            "dp_calls_per_query": agg["dp_calls"] / (nq * len(sts)),
             "dp_abandoned_frac": agg["dp_abandoned"] / max(agg["dp_calls"], 1),
             "lb_pruned_frac": (agg["lb_pruned"] + agg["lb_pruned_late"]) / max(agg["pairs"], 1),
-            "dp_cells_per_query": agg["dp_cells"] / (N_QUERIES * len(sts)),
+            "dp_cells_per_query": agg["dp_cells"] / (nq * len(sts)),
+            "seed_cells_per_query": agg["seed_cells"] / (nq * len(sts)),
             "reranked": agg["reranked"],
         }
     launches = sum(s["launches"] for _, s in collected)
@@ -273,15 +290,16 @@ def run_gpu(args):
     # end to end through the public API with host buffers: H2D of queries and
     # D2H of results inside the timed region
     q_pin = torch.from_numpy(q_host).pin_memory()
-    ids_h = torch.empty((N_QUERIES, K), dtype=torch.int64).pin_memory()
-    dst_h = torch.empty((N_QUERIES, K), dtype=torch.float32).pin_memory()
-    cnt_h = torch.empty(N_QUERIES, dtype=torch.int64).pin_memory()
+    ids_h = torch.empty((nq, K), dtype=torch.int64).pin_memory()
+    dst_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty(nq, dtype=torch.int64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for kind in kinds:
-            db.scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, out=(ids_h, dst_h, cnt_h))
+            db.scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
+                    out=(ids_h, dst_h, cnt_h))
     barrier()
     e2e_dt = time.perf_counter() - t0
     if world > 1:
@@ -290,19 +308,19 @@ def run_gpu(args):
         e2e_dt = float(t.item())
     h2d = (q_host.nbytes + q_off.nbytes) * len(kinds)
     d2h = (ids_h.numel() * 8 + dst_h.numel() * 4 + cnt_h.numel() * 8) * len(kinds)
-    e2e = {"value": N_QUERIES * len(kinds) * e2e_steps * world / e2e_dt, "unit": "queries/s",
+    e2e = {"value": nq * len(kinds) * e2e_steps * world / e2e_dt, "unit": "queries/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # the plain form: one query per launch sequence, first 50 queries
     plain = {}
-    if rank == 0:
-        nplain = 50
+    if rank == 0 and not args.no_plain:
+        nplain = min(50, nq)
         qp = q_dev[: int(q_off[nplain])]
         qpo = q_off_t[: nplain + 1]
         for kind in kinds:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            db.scan(qp, qpo, k=K, band=BAND, distance=kind, query_batch=1)
+            db.scan(qp, qpo, k=K, band=BAND, distance=kind, query_batch=1, seed=kw.SEED_GREEDY)
             torch.cuda.synchronize()
             plain["DTW" if kind == kw.DTW else "DK"] = nplain / (time.perf_counter() - t0)
 
@@ -313,12 +331,13 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH, "d": D,
-                       "queries_per_gpu": N_QUERIES, "k": K, "band": BAND,
-                       "distances": ["DTW", "DK"], "seed": "greedy upper bound (Section 4.3)",
+                       "queries_per_gpu": nq, "k": K, "band": BAND,
+                       "distances": ["DTW" if k_ == kw.DTW else "DK" for k_ in kinds],
+                       "seed": SEED_DESC[args.seed],
                        "batched": True, "l2": "inputs larger than L2 (307 MB database)",
                        "parallelism": f"replicated database, queries sharded x{world}"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-            "per_distance": detail, "plain_scan_queries_per_s": plain,
+            "per_distance": detail, "plain_scan_queries_per_s": plain, "dp_shape": shapes,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
@@ -337,6 +356,12 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", default="lb", choices=["greedy", "lb", "none"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--queries", type=int, default=N_QUERIES,
+                    help="queries per GPU (smaller values only for profiling captures)")
+    ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

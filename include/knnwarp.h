@@ -78,7 +78,12 @@ typedef enum {
      * attached to the database (knn_encoder_attach). */
     KNN_SEED_LEARNED = 1,
     /* No pre-pass: the threshold starts at +inf. */
-    KNN_SEED_NONE = 2
+    KNN_SEED_NONE = 2,
+    /* LB_Box-ordered proposal: LB_Box is computed for every series first, the
+     * seed_count series with the lowest bound are scored exactly, and the
+     * k-th best exact distance becomes the threshold against which the rest
+     * are filtered (the plain ordering, without an encoder). */
+    KNN_SEED_LB = 3
 } knn_seed_mode;
 
 typedef struct {
@@ -104,7 +109,8 @@ typedef struct {
     int64_t pairs;           /* (query, series) pairs considered                 */
     int64_t band_infeasible; /* pairs with |m - n| > r                           */
     int64_t ub_walks;        /* greedy upper-bound walks run                     */
-    int64_t seeds;           /* learned proposals scored exactly                 */
+    int64_t seeds;           /* proposals scored exactly before the filter       */
+    int64_t seed_cells;      /* DP cells evaluated for the proposals             */
     int64_t lb_pruned;       /* pruned by LB_Box before the DP queue             */
     int64_t lb_pruned_late;  /* pruned by LB_Box at DP start (tighter threshold) */
     int64_t dp_calls;        /* dynamic programs started                         */
@@ -163,6 +169,35 @@ KNN_API knn_status knn_scan_simple(const float *query, int64_t m, const float *d
                                    const int64_t *lengths, int64_t n_series, int32_t d,
                                    float band, int32_t k, float eps, int32_t distance,
                                    int64_t *ids, float *dist, int64_t *count);
+
+/* ---------------------------------------------------------------------- */
+/* Shape of the banded dynamic program and its autotuner                    */
+/*                                                                          */
+/* The DP assigns G lanes (a power of two <= 32) to one (query, series)      */
+/* pair and P band diagonals to each lane (2P cells per lane per two        */
+/* anti-diagonals); G*P >= r+1 must hold.  A shape is chosen per            */
+/* (distance, r, n) key, r the band radius and n the longest series of a    */
+/* length bucket.  Without tuning, a cost model picks it.                   */
+
+/* Time every compiled shape for each length bucket on the given queries
+ * (one full scan per shape, each bucket's DP launch timed with CUDA events)
+ * and keep the fastest in `db` for later scans with the same distance,
+ * band and query lengths.  cache_path (nullable): a JSON file of previous
+ * results (one entry per device name, d and key); keys found there are not
+ * re-timed, and the file is rewritten with the new results.  params->k > 0.
+ * queries/q_offsets as in knn_scan. */
+KNN_API knn_status knn_autotune(knn_db *db, const float *queries, const int64_t *q_offsets,
+                                int32_t n_queries, const knn_params *params,
+                                const char *cache_path, void *stream);
+/* Force the shape for one key (P must be compiled for the database's d). */
+KNN_API knn_status knn_set_dp_shape(knn_db *db, int32_t distance, int32_t r, int32_t n,
+                                    int32_t P, int32_t G);
+/* The shape a scan would use for a key (tuned, forced, or the model's). */
+KNN_API knn_status knn_get_dp_shape(knn_db *db, int32_t distance, int32_t r, int32_t n,
+                                    int32_t *P, int32_t *G);
+/* Compiled P values for dimensionality d: writes up to cap of them to
+ * P_list (nullable) and returns how many exist. */
+KNN_API int32_t knn_dp_shapes(int32_t d, int32_t *P_list, int32_t cap);
 
 /* ---------------------------------------------------------------------- */
 /* Components (each is one step of the scan, exposed for verification and  */

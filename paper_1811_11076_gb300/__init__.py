@@ -28,6 +28,7 @@ DK = 1
 SEED_GREEDY = 0
 SEED_LEARNED = 1
 SEED_NONE = 2
+SEED_LB = 3
 
 STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA",
           4: "KNN_ERR_TIMEOUT", 5: "KNN_ERR_CAPACITY", 6: "KNN_ERR_UNSUPPORTED"}
@@ -35,7 +36,8 @@ STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA"
 # every symbol include/knnwarp.h declares
 EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
-           "knn_last_error", "knn_version")
+           "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
+           "knn_dp_shapes")
 
 
 class KnnError(RuntimeError):
@@ -53,7 +55,7 @@ class Params(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("pairs", C.c_int64), ("band_infeasible", C.c_int64), ("ub_walks", C.c_int64),
-                ("seeds", C.c_int64), ("lb_pruned", C.c_int64), ("lb_pruned_late", C.c_int64),
+                ("seeds", C.c_int64), ("seed_cells", C.c_int64), ("lb_pruned", C.c_int64), ("lb_pruned_late", C.c_int64),
                 ("dp_calls", C.c_int64), ("dp_abandoned", C.c_int64), ("dp_cells", C.c_int64),
                 ("reranked", C.c_int64), ("launches", C.c_int64), ("ms_total", C.c_double),
                 ("ms_seed", C.c_double), ("ms_lb", C.c_double), ("ms_dp", C.c_double),
@@ -90,6 +92,10 @@ def lib() -> C.CDLL:
     L.knn_greedy_ub.argtypes = [vp, vp, C.c_int64, C.c_float, C.c_int32, vp, vp]
     L.knn_pairwise.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_float,
                                C.c_int32, vp, vp, vp]
+    L.knn_autotune.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(Params), C.c_char_p, vp]
+    L.knn_set_dp_shape.argtypes = [vp] + [C.c_int32] * 5
+    L.knn_get_dp_shape.argtypes = [vp] + [C.c_int32] * 3 + [C.POINTER(C.c_int32)] * 2
+    L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
     for f in EXPORTS:
         if f not in ("knn_status_string", "knn_last_error", "knn_version"):
             getattr(L, f).restype = C.c_int
@@ -212,6 +218,25 @@ class KnnDB:
         res = (ids, dist) if k > 0 else (ids, dist, counts)
         return res + (st.as_dict(),) if stats else res
 
+    def autotune(self, queries, q_offsets, *, k: int = 10, band: float = 0.1,
+                 distance: int = DTW, seed: int = 3, cache_path: str | None = None,
+                 stream=None):
+        """Time every compiled DP shape per length bucket; keep the fastest."""
+        queries = _f32(queries)
+        q_offsets = _i64(q_offsets)
+        p = Params(k=k, band=band, distance=distance, seed_mode=seed)
+        _check(lib().knn_autotune(self._h, _ptr(queries), _ptr(q_offsets),
+                                  int(q_offsets.shape[0] - 1), C.byref(p),
+                                  cache_path.encode() if cache_path else None, _stream(stream)))
+
+    def set_dp_shape(self, distance: int, r: int, n: int, P: int, G: int):
+        _check(lib().knn_set_dp_shape(self._h, distance, r, n, P, G))
+
+    def get_dp_shape(self, distance: int, r: int, n: int):
+        P, G = C.c_int32(), C.c_int32()
+        _check(lib().knn_get_dp_shape(self._h, distance, r, n, C.byref(P), C.byref(G)))
+        return P.value, G.value
+
     def lb_box(self, query, band: float, form: int = 0, stream=None):
         """LB_Box of every series against the query envelope (device tensor out)."""
         import torch
@@ -229,6 +254,14 @@ class KnnDB:
         _check(lib().knn_greedy_ub(self._h, _ptr(query), int(query.shape[0]), band, form,
                                    _ptr(out), _stream(stream)))
         return out
+
+
+def dp_shapes(d: int) -> list[int]:
+    """Compiled P values (band cells per lane) for dimensionality d."""
+    n = lib().knn_dp_shapes(d, None, 0)
+    buf = (C.c_int32 * max(n, 1))()
+    lib().knn_dp_shapes(d, C.cast(buf, C.c_void_p), n)
+    return list(buf[:n])
 
 
 def envelope(t, r: int, length: int | None = None, stream=None):

@@ -336,6 +336,7 @@ extern "C" knn_status knn_pairwise(const float *a, const int64_t *a_off, const f
         x.mu_keep = 1.f;
         x.mu_prune = 1.f;
         x.out_pair = OUT.as<float>();
+        x.cells_stat = STAT_DP_CELLS;
         x.stats = ct->stats;
         x.status = &ct->status;
         int dev = 0, nsm = 0;
@@ -352,12 +353,10 @@ extern "C" knn_status knn_pairwise(const float *a, const int64_t *a_off, const f
     }
     if (out_f64) {
         const int row = 2 * max_r + 1;
-        const int threads = (int)std::min<int64_t>(std::max<int64_t>(n_pairs, 64), 16384) / 64 * 64;
-        DevBuf scratch;
-        if ((s = scratch.ensure(sizeof(double) * 2 * row * (size_t)threads)))
-            return s;
-        launch_pairwise64(a, a_off, b, b_off, pa, pb, n_pairs, d, band, distance,
-                          out_f64, scratch.as<double>(), row, threads, st);
+        if ((size_t)3 * (row + 2) * sizeof(double) > 200 * 1024)
+            return set_error(KNN_ERR_UNSUPPORTED, "band too wide for the FP64 pair program");
+        launch_pairwise64(a, a_off, b, b_off, pa, pb, n_pairs, d, band, distance, out_f64, row,
+                          st);
         e = cudaStreamSynchronize(st);
         if (e == cudaSuccess)
             e = cudaGetLastError();

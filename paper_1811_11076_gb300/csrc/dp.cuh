@@ -23,6 +23,18 @@
 // compile-time positions inside a U-times unrolled step loop.  Cells outside
 // the band get +inf through the FMA accumulator of their cost (mask 0/inf).
 //
+// Start and end.  Every pair is swept in whole blocks of U steps, and the
+// sweep starts at a step s_start <= 0 chosen so that the end cell
+// (m-1, n-1) falls on the last step of a block; the result is then read once
+// per block, outside the unrolled loop.  The steps before 0 run over a
+// virtual prefix: rows i < 0 and columns j < 0 read a sentinel point of huge
+// coordinates, so a cell with both indices negative costs exactly 0 and a
+// cell with one negative index costs about 1e36 (or +inf).  With every
+// in-band cell of the first step in the negative quadrant and set to 0,
+// cell (0,0) receives min(...) = 0 from (-1,-1) and every real cell receives
+// the same value as in the plain recurrence (the prefix can only reach it
+// through (0,0)).
+//
 // Early abandoning (Section 4, first paragraph; Algorithm 3's empty active
 // set for DK): the last two anti-diagonals form a cut of every warping path,
 // and costs are non-negative, so their minimum bounds D(m-1,n-1) from below.
@@ -38,6 +50,21 @@
 namespace knn {
 
 constexpr int DP_THREADS = 128;
+constexpr float DP_PREFIX = 1e18f;  // sentinel coordinate of the virtual prefix
+
+// Point idx of a series (clamped to its last point), or the sentinel point
+// for idx < 0.
+template <int D>
+__device__ __forceinline__ void load_point_prefix(const float *p, int idx, int last,
+                                                  float (&v)[D])
+{
+    load_point<D>(p + clampi(idx, 0, last) * D, v);
+    if (idx < 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+            v[k] = DP_PREFIX;
+    }
+}
 
 template <int D, int P, int KIND>
 __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
@@ -67,7 +94,6 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
     int s_f = -1, fin_lane = 0, fin_slot = 0, fin_odd = 0;
     int qi = 0, ci = 0, cur_idx = 0;
     bool active = false, done = false;
-    float result = KNN_INF;
     int s0 = 0;
 
     int wbase = 0, wcur = 32;
@@ -123,22 +149,24 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                             const int de = lo + 2 * P * lam + 2 * e;
                             mE[e] = (abs(de) <= r) ? 0.f : KNN_INF;
                             mO[e] = (abs(de + 1) <= r) ? 0.f : KNN_INF;
-                            E[e] = (de == 0) ? 0.f : KNN_INF;
-                            O[e] = KNN_INF;
+                            E[e] = mE[e];  // virtual prefix: in-band cells are 0
+                            O[e] = mO[e];
                         }
                         const int off = (n - m) - lo;
                         fin_lane = off / (2 * P);
                         fin_slot = (off % (2 * P)) >> 1;
                         fin_odd = off & 1;
                         s_f = (m + n - 2) >> 1;
+                        // first step: all in-band cells in the negative quadrant,
+                        // and a whole number of U-step blocks up to s_f
+                        const int smin = -((r + 1) >> 1) - 1;
+                        const int nsteps = (s_f - smin + 1 + U - 1) / U * U;
+                        s0 = s_f - nsteps + 1;
 #pragma unroll
                         for (int p = 0; p < U; ++p) {
-                            const int row = -h - ((U - p) % U);
-                            load_point<D>(qp + clampi(row, 0, m - 1) * D, qw[p]);
-                            load_point<D>(xp + clampi(h + p, 0, n - 1) * D, xw[p]);
+                            load_point_prefix<D>(qp, s0 - h - ((U - p) % U), m - 1, qw[p]);
+                            load_point_prefix<D>(xp, s0 + h + p, n - 1, xw[p]);
                         }
-                        s0 = 0;
-                        result = KNN_INF;
                         active = true;
                         st_calls += (lam == 0);
                     }
@@ -153,8 +181,8 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int s = s0 + u;
-            load_point<D>(qp + clampi(s - h, 0, m - 1) * D, qw[u]);
-            load_point<D>(xp + clampi(s + h + P, 0, n - 1) * D, xw[(u + P) % U]);
+            load_point_prefix<D>(qp, s - h, m - 1, qw[u]);
+            load_point_prefix<D>(xp, s + h + P, n - 1, xw[(u + P) % U]);
 
             float up = __shfl_up_sync(KNN_FULL_MASK, O[P - 1], 1, G);
             up = (lam == 0) ? KNN_INF : up;
@@ -175,16 +203,15 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                 const float mn = fminf(fminf(E[e], right), O[e]);
                 O[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
             }
-            if (s == s_f && lam == fin_lane) {
-                float v = KNN_INF;
-#pragma unroll
-                for (int e = 0; e < P; ++e)
-                    if (e == fin_slot)
-                        v = fin_odd ? O[e] : E[e];
-                result = v;
-            }
         }
         s0 += U;
+
+        // the end cell, valid when this block ended on step s_f
+        float result = KNN_INF;
+#pragma unroll
+        for (int e = 0; e < P; ++e)
+            if (e == fin_slot)
+                result = fin_odd ? O[e] : E[e];
 
         // ---- finish or abandon (group-wide) ------------------------------------
         const float res = __shfl_sync(KNN_FULL_MASK, result, gbase + fin_lane);
@@ -197,7 +224,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
         if (active) {
             const float thr = a.out_pair ? KNN_INF : ld_volatile_f32(a.thr + qi);
             const float lim = thr * a.mu_keep;
-            const bool finished = (s0 - 1 >= s_f);
+            const bool finished = (s0 - 1 == s_f);
             if (finished) {
                 if (lam == 0) {
                     // exact band cells of the m x n matrix
@@ -252,7 +279,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
     if (lane == 0 && a.stats) {
         atomicAdd(a.stats + STAT_DP_CALLS, st_calls);
         atomicAdd(a.stats + STAT_DP_ABANDONED, st_aband);
-        atomicAdd(a.stats + STAT_DP_CELLS, st_cells);
+        atomicAdd(a.stats + a.cells_stat, st_cells);
         atomicAdd(a.stats + STAT_LB_PRUNED_LATE, st_pruned);
     }
 }

@@ -17,49 +17,65 @@ namespace knn {
 
 constexpr int FIN_THREADS = 128;
 
-// Banded DP in FP64 for one pair, row by row; rows are band offsets
-// b = j - i + r in [0, 2r].  kind 0: DTW (sum of squared costs); kind 1: DK^2
-// (max of squared costs).  Products and sums are rounded separately (no
-// fused multiply-add) and coordinates are accumulated in order, exactly as
-// a plain double-precision evaluation of the definition does.
-__device__ double dp_fp64(const float *s, int m, const float *t, int n, int d, int r, int kind,
-                          double *prev, double *cur)
+// Banded DP in FP64 for one pair, computed by one warp along anti-diagonals
+// t = i + j: every cell of an anti-diagonal is independent, lanes take the
+// band diagonals delta = j - i of the right parity in strides of 64, and the
+// two previous anti-diagonals live in shared memory (indexed by delta + r + 1,
+// with an infinite sentinel on both sides).  kind 0: DTW (sum of squared
+// costs); kind 1: DK^2 (max of squared costs).  Each cell applies exactly the
+// operations of the recurrence (products and sums rounded separately, no
+// fused multiply-add, coordinates in order), so the value equals that of a
+// sequential double-precision evaluation regardless of the sweep order.
+// Shared memory: 3 * (2r + 3) doubles.  Returns the value in lane 0 and all
+// lanes.
+__device__ double dp_fp64_warp(const float *s, int m, const float *t, int n, int d, int r,
+                               int kind, double *buf)
 {
+    const int lane = threadIdx.x & 31;
     if (abs(m - n) > r)
         return (double)KNN_INF;
-    const int W = 2 * r + 1;
-    for (int b = 0; b < W; ++b)
-        prev[b] = (double)KNN_INF;
-    for (int i = 0; i < m; ++i) {
-        for (int b = 0; b < W; ++b) {
-            const int j = i + b - r;
-            if (j < 0 || j >= n) {
-                cur[b] = (double)KNN_INF;
-                continue;
+    const int W = 2 * r + 3;
+    double *A = buf, *B = buf + W, *Cc = buf + 2 * W;  // t-2, t-1, t
+    for (int b = lane; b < 3 * W; b += 32)
+        buf[b] = (double)KNN_INF;
+    __syncwarp();
+    const int tmax = m + n - 2;
+    for (int tt = 0; tt <= tmax; ++tt) {
+        // diagonals delta in [-r, r] with delta = tt (mod 2)
+        const int d0 = -r + (((tt + r) & 1) ? 1 : 0);
+        for (int dl = d0 + 2 * lane; dl <= r; dl += 64) {
+            const int i2 = tt - dl, j2 = tt + dl;  // 2i, 2j
+            const int i = i2 >> 1, j = j2 >> 1;
+            double v = (double)KNN_INF;
+            if (i >= 0 && i < m && j >= 0 && j < n) {
+                double c = 0.0;
+                for (int k = 0; k < d; ++k) {
+                    const double df =
+                        __dsub_rn((double)s[(int64_t)i * d + k], (double)t[(int64_t)j * d + k]);
+                    c = __dadd_rn(c, __dmul_rn(df, df));
+                }
+                if (tt == 0) {
+                    v = c;
+                } else {
+                    const int x = dl + r + 1;
+                    const double best = fmin(fmin(B[x - 1], B[x + 1]), A[x]);
+                    v = kind == 0 ? __dadd_rn(c, best) : fmax(c, best);
+                }
             }
-            double c = 0.0;
-            for (int k = 0; k < d; ++k) {
-                const double df =
-                    __dsub_rn((double)s[(int64_t)i * d + k], (double)t[(int64_t)j * d + k]);
-                c = __dadd_rn(c, __dmul_rn(df, df));
-            }
-            double v;
-            if (i == 0 && j == 0) {
-                v = c;
-            } else {
-                const double left = b > 0 ? cur[b - 1] : (double)KNN_INF;      // (i, j-1)
-                const double low = b + 1 < W ? prev[b + 1] : (double)KNN_INF;  // (i-1, j)
-                const double diag = prev[b];                                    // (i-1, j-1)
-                const double best = fmin(fmin(left, low), diag);
-                v = kind == 0 ? __dadd_rn(c, best) : fmax(c, best);
-            }
-            cur[b] = v;
+            Cc[dl + r + 1] = v;
         }
-        double *tmp = prev;
-        prev = cur;
-        cur = tmp;
+        __syncwarp();
+        // rotate: the new t-2 is the old t-1; reset the outgoing row to +inf
+        double *old = A;
+        A = B;
+        B = Cc;
+        Cc = old;
+        for (int b = lane; b < W; b += 32)
+            Cc[b] = (double)KNN_INF;
+        __syncwarp();
     }
-    return prev[(n - 1) - (m - 1) + r];
+    // the end cell (m-1, n-1) lies on anti-diagonal tmax, now in B
+    return B[(n - m) + r + 1];
 }
 
 // ---------------------------------------------------------------------------
@@ -127,9 +143,23 @@ __global__ void __launch_bounds__(FIN_THREADS) fin_mark_kernel(const FinArgs a)
     const float w = a.rerank_rel;
     const float pivot = knn_mode ? (cnt >= a.k ? key_dist(keys[a.k - 1]) : KNN_INF) : a.eps_int;
     double *vals = a.fin_vals + (size_t)qb * a.fin_width;
+    // k-NN: the cut can only move if a second entry shares the boundary band
+    __shared__ int s_band;
+    if (tid == 0)
+        s_band = 0;
+    __syncthreads();
+    if (knn_mode && pivot < KNN_INF)
+        for (int i = tid; i < cnt; i += blockDim.x) {
+            const float di = key_dist(keys[i]);
+            if (di >= pivot * (1.f - w) && di <= pivot * (1.f + w) && di != pivot)
+                atomicAdd(&s_band, 1);
+        }
+    __syncthreads();
+    const bool band_matters = !knn_mode || s_band > 0;
     for (int i = tid; i < cnt; i += blockDim.x) {
         const float di = key_dist(keys[i]);
-        bool nd = pivot < KNN_INF && di >= pivot * (1.f - w) && di <= pivot * (1.f + w);
+        bool nd = band_matters && pivot < KNN_INF && di >= pivot * (1.f - w) &&
+                  di <= pivot * (1.f + w);
         if (knn_mode && i <= a.k) {
             if (i > 0) {
                 const float dp = key_dist(keys[i - 1]);
@@ -152,12 +182,13 @@ __global__ void __launch_bounds__(FIN_THREADS) fin_mark_kernel(const FinArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// 2. rescore: one thread per picked entry
+// 2. rescore: one warp (one block) per picked entry
 
-__global__ void fin_rescore_kernel(const FinArgs a)
+__global__ void __launch_bounds__(32) fin_rescore_kernel(const FinArgs a)
 {
+    extern __shared__ double rbuf[];
     const int n_rer = min(*a.rer_count, a.rer_cap);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_rer; e += gridDim.x * blockDim.x) {
+    for (int e = blockIdx.x; e < n_rer; e += gridDim.x) {
         const int2 it = a.rer_list[e];
         const int qb = it.x, i = it.y;
         const unsigned long long key = a.k > 0 ? a.slots[(size_t)qb * a.kslots + i]
@@ -167,13 +198,15 @@ __global__ void fin_rescore_kernel(const FinArgs a)
         const int n = a.db_len_by_id[id];
         const int r = band_radius(m, n, a.band);
         if (2 * r + 1 > a.rer_row) {
-            atomicOr(a.status, KNN_DEV_BAD_SHAPE);
+            if (threadIdx.x == 0)
+                atomicOr(a.status, KNN_DEV_BAD_SHAPE);
             continue;
         }
-        double *rows = a.rer_scratch + (size_t)e * 2 * a.rer_row;
-        const double v = dp_fp64(a.q + a.q_off[qb], m, a.db + a.db_off_by_id[id], n, a.d, r,
-                                 a.kind, rows, rows + a.rer_row);
-        a.fin_vals[(size_t)qb * a.fin_width + i] = v;
+        const double v = dp_fp64_warp(a.q + a.q_off[qb], m, a.db + a.db_off_by_id[id], n, a.d, r,
+                                      a.kind, rbuf);
+        if (threadIdx.x == 0)
+            a.fin_vals[(size_t)qb * a.fin_width + i] = v;
+        __syncwarp();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats)
         atomicAdd(a.stats + STAT_RERANKED, (unsigned long long)n_rer);
@@ -257,6 +290,8 @@ __global__ void __launch_bounds__(FIN_THREADS) fin_out_kernel(const FinArgs a)
 
 void fin_init_attributes()
 {
+    cudaFuncSetAttribute(fin_rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     cudaFuncSetAttribute(fin_mark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(fin_out_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -266,45 +301,45 @@ void launch_finalize(const FinArgs &a, cudaStream_t st)
     const size_t smem_mark = (size_t)a.sort_cap * sizeof(unsigned long long);
     const size_t smem_out = (size_t)a.sort_cap * (sizeof(unsigned long long) + sizeof(double));
     fin_mark_kernel<<<a.nq, FIN_THREADS, smem_mark, st>>>(a);
-    fin_rescore_kernel<<<64, 64, 0, st>>>(a);
+    const size_t smem_rer = (size_t)3 * (a.rer_row + 2) * sizeof(double);
+    fin_rescore_kernel<<<a.rer_cap < 4096 ? a.rer_cap : 4096, 32, smem_rer, st>>>(a);
     fin_out_kernel<<<a.nq, FIN_THREADS, smem_out, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------
-// FP64 pair program (thread per pair), band rows in global scratch
+// FP64 pair program: one warp (one block) per pair
 
-__global__ void pairwise64_kernel(const float *a, const int64_t *a_off, const float *b,
-                                  const int64_t *b_off, const int64_t *pa, const int64_t *pb,
-                                  int64_t n, int d, float band, int kind, double *out,
-                                  double *scratch, int row)
+__global__ void __launch_bounds__(32) pairwise64_kernel(const float *a, const int64_t *a_off,
+                                                        const float *b, const int64_t *b_off,
+                                                        const int64_t *pa, const int64_t *pb,
+                                                        int64_t n, int d, float band, int kind,
+                                                        int row, double *out)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double *rows = scratch + tid * 2 * row;
-    for (int64_t p = tid; p < n; p += stride) {
+    extern __shared__ double pbuf[];
+    for (int64_t p = blockIdx.x; p < n; p += gridDim.x) {
         const int64_t ia = pa[p], ib = pb[p];
         const int m = (int)(a_off[ia + 1] - a_off[ia]);
         const int nn = (int)(b_off[ib + 1] - b_off[ib]);
         const int r = band_radius(m, nn, band);
-        if (2 * r + 1 > row) {
-            out[p] = -1.0;
-            continue;
-        }
-        const double v = dp_fp64(a + a_off[ia] * d, m, b + b_off[ib] * d, nn, d, r, kind, rows,
-                                 rows + row);
-        out[p] = kind == 0 ? v : sqrt(v);
+        double v = -1.0;
+        if (2 * r + 1 <= row)
+            v = dp_fp64_warp(a + a_off[ia] * d, m, b + b_off[ib] * d, nn, d, r, kind, pbuf);
+        if (threadIdx.x == 0)
+            out[p] = v < 0.0 ? v : (kind == 0 ? v : sqrt(v));
+        __syncwarp();
     }
 }
 
 void launch_pairwise64(const float *a, const int64_t *a_off, const float *b, const int64_t *b_off,
                        const int64_t *pa, const int64_t *pb, int64_t n, int d, float band,
-                       int kind, double *out, double *scratch, int row, int threads_total,
-                       cudaStream_t st)
+                       int kind, double *out, int row, cudaStream_t st)
 {
-    const int tpb = 64;
-    const int blocks = threads_total / tpb;
-    pairwise64_kernel<<<blocks, tpb, 0, st>>>(a, a_off, b, b_off, pa, pb, n, d, band, kind, out,
-                                              scratch, row);
+    const size_t smem = (size_t)3 * (row + 2) * sizeof(double);
+    cudaFuncSetAttribute(pairwise64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    const int blocks = (int)(n < 65536 ? n : 65536);
+    pairwise64_kernel<<<blocks > 0 ? blocks : 1, 32, smem, st>>>(a, a_off, b, b_off, pa, pb, n,
+                                                                 d, band, kind, row, out);
 }
 
 }  // namespace knn

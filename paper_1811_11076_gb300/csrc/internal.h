@@ -84,6 +84,41 @@ struct GreedyArgs {
 };
 void launch_greedy(const GreedyArgs &a, int d, int form, cudaStream_t st);
 
+// -- seeded scan: selection of seeds and filtering of survivors -------------
+struct SelArgs {
+    const float *score;        // [nq][score_stride] ranking score per series (bucket order)
+    int64_t score_stride;
+    float *lb_all;             // [nq][lb_stride] LB_Box per series; seeds are set to -1
+    int64_t lb_stride;
+    int n;                     // series
+    int c_base;                // index of score[0] in bucket order
+    int nq;
+    int S;                     // seeds per query
+    int2 *seed_items;
+    float *seed_lb;
+    int *n_seed;
+    int seed_cap;
+    unsigned long long *stats;
+    int *status;
+};
+void launch_select(const SelArgs &a, cudaStream_t st);
+
+struct FilterArgs {
+    const float *lb_all;
+    int64_t lb_stride;
+    int c_begin, c_end;
+    int nq;
+    const float *thr;
+    float mu_prune;
+    int2 *items;
+    float *item_lb;
+    int *n_items;
+    int64_t capacity;
+    unsigned long long *stats;
+    int *status;
+};
+void launch_filter(const FilterArgs &a, int n_sm, cudaStream_t st);
+
 // -- banded dynamic program on the survivor queue ----------------------------
 struct DpArgs {
     const int2 *items;
@@ -109,6 +144,7 @@ struct DpArgs {
     int *eps_count;
     int eps_cap;
     float *out_pair;           // pair mode: result per queue entry, no threshold
+    int cells_stat;            // statistics slot receiving the evaluated cells
     unsigned long long *stats;
     int *status;
 };
@@ -140,7 +176,6 @@ struct FinArgs {
     int2 *rer_list;            // (query, position) of entries to re-score
     int *rer_count;
     int rer_cap;
-    double *rer_scratch;       // [rer_cap][2][rer_row]
     int rer_row;               // longest band row supported (2r+1)
     // data for FP64 re-scoring (caller ids -> database rows)
     const float *db;
@@ -161,10 +196,10 @@ void launch_finalize(const FinArgs &a, cudaStream_t st);
 void fin_init_attributes();
 
 // -- pair programs (no pruning) ----------------------------------------------
+// FP64 pair program, one warp per pair; row >= 2r+1 for every pair (r <= 8000).
 void launch_pairwise64(const float *a, const int64_t *a_off, const float *b, const int64_t *b_off,
                        const int64_t *pa, const int64_t *pb, int64_t n, int d, float band,
-                       int kind, double *out, double *scratch, int row, int threads_total,
-                       cudaStream_t st);
+                       int kind, double *out, int row, cudaStream_t st);
 
 // -- small utilities ------------------------------------------------------------
 void launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st);
@@ -189,6 +224,7 @@ enum Stat : int {
     STAT_DP_ABANDONED,
     STAT_DP_CELLS,
     STAT_RERANKED,
+    STAT_SEED_CELLS,
     STAT_COUNT
 };
 

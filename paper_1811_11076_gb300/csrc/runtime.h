@@ -53,7 +53,7 @@ struct Workspace {
     DevBuf fin_valid, fin_vals, rer_list, rer_scratch;
     DevBuf out_ids, out_dist, out_counts;
     DevBuf skip;
-    DevBuf seed_items, seed_lb, scores, sel;
+    DevBuf seed_items, seed_lb, scores, sel, lb_all;
     uint64_t generation = 0;            // bumped whenever a buffer moves
 };
 
@@ -88,6 +88,11 @@ struct DpChoice {
 
 }  // namespace knn
 
+struct knn_db;
+namespace knn {
+DpChoice dp_choice(knn_db *db, int kind, int r, int n);
+}
+
 struct knn_db {
     int d = 0, deff = 0, N = 0;
     int dev = 0, n_sm = 0;
@@ -102,6 +107,9 @@ struct knn_db {
     std::map<knn::GraphKey, cudaGraphExec_t> graphs;
     cudaStream_t cap_stream = nullptr;    // private stream used only to capture graphs
     std::map<std::tuple<int, int, int>, knn::DpChoice> tuned;  // (kind, r, n) -> config
+    bool tuning = false;                  // autotuner running: one DP segment per bucket
+    std::vector<double> seg_ms;           // profile: DP time per segment of the last scan
+    std::vector<int> seg_first_bucket;    // first bucket of each segment of the last scan
     ~knn_db()
     {
         for (auto &g : graphs)

@@ -35,6 +35,9 @@ struct Plan {
     Margins mg{};
     float eps_int = 0.f;
     int rer_row = 0, rer_cap = 0;
+    bool seeded = false;
+    int S = 0;                  // seeds per query
+    DpChoice seed_dp{};
 };
 
 knn_status grow(Workspace &ws, DevBuf &b, size_t bytes)
@@ -53,7 +56,9 @@ int next_pow2i(int v)
     return p;
 }
 
-DpChoice dp_choice(knn_db *db, int kind, int r, int n)
+}  // namespace
+
+DpChoice knn::dp_choice(knn_db *db, int kind, int r, int n)
 {
     auto it = db->tuned.find(std::make_tuple(kind, r, n));
     if (it != db->tuned.end())
@@ -62,6 +67,8 @@ DpChoice dp_choice(knn_db *db, int kind, int r, int n)
     choose_dp_config(db->deff, r, n, &c.P, &c.G);
     return c;
 }
+
+namespace {
 
 knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int nq,
                      const knn_params &p, Plan &pl)
@@ -96,7 +103,8 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
         if (c.P == 0)
             return set_error(KNN_ERR_UNSUPPORTED, "band too wide for the compiled DP variants");
         const int64_t cap = (int64_t)nq * (b.c_end - b.c_begin);
-        if (!pl.segs.empty() && pl.segs.back().P == c.P && pl.segs.back().G == c.G) {
+        if (!pl.segs.empty() && pl.segs.back().P == c.P && pl.segs.back().G == c.G &&
+            !db->tuning) {
             pl.segs.back().b_end = (int)bi + 1;
             pl.segs.back().cap += cap;
         } else if ((int)pl.segs.size() == MAX_SEG) {
@@ -136,7 +144,18 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
     pl.mg = margins_for(p.distance, pl.max_m + db->max_len, db->deff);
     pl.eps_int = p.distance == KNN_DK ? p.eps * p.eps : p.eps;
     pl.rer_row = 2 * band_radius(pl.max_m, db->max_len, p.band) + 1;
+    if ((size_t)3 * (pl.rer_row + 2) * sizeof(double) > 200 * 1024)
+        return set_error(KNN_ERR_UNSUPPORTED, "band too wide for FP64 re-scoring (r > 4000)");
     pl.rer_cap = 1024 + 8 * nq;
+    pl.seeded = p.k > 0 && (p.seed_mode == KNN_SEED_LB || p.seed_mode == KNN_SEED_LEARNED);
+    if (pl.seeded) {
+        pl.S = p.seed_count > 0 ? p.seed_count : std::max(64, 4 * p.k);
+        pl.S = std::max(pl.S, p.k);
+        pl.seed_dp = dp_choice(db, p.distance, band_radius(pl.max_m, db->max_len, p.band),
+                               db->max_len);
+        if (pl.seed_dp.P == 0)
+            return set_error(KNN_ERR_UNSUPPORTED, "band too wide for the compiled DP variants");
+    }
     return KNN_OK;
 }
 
@@ -164,18 +183,57 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(fin_valid, sizeof(int) * nq);
     G_(fin_vals, sizeof(double) * nq * std::max<int64_t>(pl.kslots, pl.eps_cap));
     G_(rer_list, sizeof(int2) * pl.rer_cap);
-    G_(rer_scratch, sizeof(double) * pl.rer_cap * 2 * pl.rer_row);
     G_(out_ids, sizeof(int64_t) * nq * pl.width);
     G_(out_dist, sizeof(float) * nq * pl.width);
     G_(out_counts, sizeof(int64_t) * nq);
+    if (pl.seeded) {
+        G_(lb_all, sizeof(float) * nq * (size_t)db->N);
+        G_(seed_items, sizeof(int2) * nq * (size_t)pl.S);
+        G_(seed_lb, sizeof(float) * nq * (size_t)pl.S);
+    }
 #undef G_
     return KNN_OK;
 }
 
-// Optional stage events: [0] start, [1] after seeding, [2] after LB, [3] after
-// DP, [4] after finalise.
+DpArgs dp_args(knn_db *db, const Plan &pl, const knn_params &p, const int2 *items,
+              const float *item_lb, const int *n_items, int64_t cap, int *head)
+{
+    Workspace &ws = db->ws;
+    Ctrl *ctrl = ws.ctrl.as<Ctrl>();
+    DpArgs a{};
+    a.items = items;
+    a.item_lb = item_lb;
+    a.n_items = n_items;
+    a.items_cap = cap;
+    a.head = head;
+    a.db = db->data.as<float>();
+    a.db_off = db->off.as<int64_t>();
+    a.db_len = db->len.as<int>();
+    a.db_id = db->id.as<int>();
+    a.q = ws.qbuf.as<float>();
+    a.q_off = ws.q_off.as<int64_t>();
+    a.q_len = ws.q_len.as<int>();
+    a.band = p.band;
+    a.thr = ws.thr.as<float>();
+    a.mu_keep = pl.mg.mu_keep;
+    a.mu_prune = pl.mg.mu_prune;
+    a.k = p.k;
+    a.kslots = pl.kslots;
+    a.slots = ws.slots.as<unsigned long long>();
+    a.eps_list = ws.eps_list.as<unsigned long long>();
+    a.eps_count = ws.eps_count.as<int>();
+    a.eps_cap = (int)pl.eps_cap;
+    a.stats = ctrl->stats;
+    a.status = &ctrl->status;
+    return a;
+}
+
+// Optional stage events: [0] start, [1] after the greedy pre-pass, [2] after
+// the LB_Box stream, [3] after seed selection and seed programs, [4] after the
+// survivor filter, [5] after the DP, [6] after finalise.
 struct StageEvents {
-    cudaEvent_t ev[5];
+    cudaEvent_t ev[7];
+    cudaEvent_t seg[MAX_SEG + 1];
 };
 
 // All launches of one batch; capturable (no host synchronisation, no
@@ -235,7 +293,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     if (sev)
         cudaEventRecord(sev->ev[1], st);
 
-    // envelope + LB_Box stream per bucket
+    // envelope + LB_Box stream per bucket (seeded: store every bound)
     for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
         const Bucket &b = db->buckets[bi];
         const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];
@@ -268,10 +326,15 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         l.env_floats = (int)((int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
         l.thr = ws.thr.as<float>();
         l.mu_prune = pl.mg.mu_prune;
-        l.items = ws.items.as<int2>() + sg.base;
-        l.item_lb = ws.item_lb.as<float>() + sg.base;
-        l.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];
-        l.capacity = sg.cap;
+        if (pl.seeded) {
+            l.out_lb = ws.lb_all.as<float>();
+            l.out_lb_stride = db->N;
+        } else {
+            l.items = ws.items.as<int2>() + sg.base;
+            l.item_lb = ws.item_lb.as<float>() + sg.base;
+            l.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];
+            l.capacity = sg.cap;
+        }
         l.stats = stats;
         l.status = &ctrl->status;
         launch_lb(l, db->deff, kind, db->n_sm, st);
@@ -280,41 +343,76 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     if (sev)
         cudaEventRecord(sev->ev[2], st);
 
+    if (pl.seeded) {
+        // seeds: the S series of lowest LB_Box per query, scored exactly first
+        SelArgs sa{};
+        sa.score = ws.lb_all.as<float>();
+        sa.score_stride = db->N;
+        sa.lb_all = ws.lb_all.as<float>();
+        sa.lb_stride = db->N;
+        sa.n = db->N;
+        sa.c_base = 0;
+        sa.nq = nq;
+        sa.S = pl.S;
+        sa.seed_items = ws.seed_items.as<int2>();
+        sa.seed_lb = ws.seed_lb.as<float>();
+        sa.n_seed = &ctrl->n_seed;
+        sa.seed_cap = nq * pl.S;
+        sa.stats = stats;
+        sa.status = &ctrl->status;
+        launch_select(sa, st);
+        DpArgs a = dp_args(db, pl, p, ws.seed_items.as<int2>(), ws.seed_lb.as<float>(),
+                           &ctrl->n_seed, (int64_t)nq * pl.S, &ctrl->seed_head);
+        a.G = pl.seed_dp.G;
+        a.cells_stat = STAT_SEED_CELLS;
+        const int occ = dp_max_blocks_per_sm(db->deff, pl.seed_dp.P, kind);
+        launch_dp(a, db->deff, pl.seed_dp.P, kind, db->n_sm * std::max(occ, 1), st);
+        launches += 2;
+    }
+    if (sev)
+        cudaEventRecord(sev->ev[3], st);
+    if (pl.seeded) {
+        for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
+            const Bucket &b = db->buckets[bi];
+            const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];
+            FilterArgs fa{};
+            fa.lb_all = ws.lb_all.as<float>();
+            fa.lb_stride = db->N;
+            fa.c_begin = b.c_begin;
+            fa.c_end = b.c_end;
+            fa.nq = nq;
+            fa.thr = ws.thr.as<float>();
+            fa.mu_prune = pl.mg.mu_prune;
+            fa.items = ws.items.as<int2>() + sg.base;
+            fa.item_lb = ws.item_lb.as<float>() + sg.base;
+            fa.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];
+            fa.capacity = sg.cap;
+            fa.stats = stats;
+            fa.status = &ctrl->status;
+            launch_filter(fa, db->n_sm, st);
+            ++launches;
+        }
+    }
+    if (sev)
+        cudaEventRecord(sev->ev[4], st);
+
     // banded DP over each segment's survivors
     for (size_t si = 0; si < pl.segs.size(); ++si) {
         const Segment &sg = pl.segs[si];
-        DpArgs a{};
-        a.items = ws.items.as<int2>() + sg.base;
-        a.item_lb = ws.item_lb.as<float>() + sg.base;
-        a.n_items = &ctrl->seg_count[si];
-        a.items_cap = sg.cap;
-        a.head = &ctrl->seg_head[si];
-        a.db = db->data.as<float>();
-        a.db_off = db->off.as<int64_t>();
-        a.db_len = db->len.as<int>();
-        a.db_id = db->id.as<int>();
-        a.q = ws.qbuf.as<float>();
-        a.q_off = ws.q_off.as<int64_t>();
-        a.q_len = ws.q_len.as<int>();
-        a.band = p.band;
+        if (sev)
+            cudaEventRecord(sev->seg[si], st);
+        DpArgs a = dp_args(db, pl, p, ws.items.as<int2>() + sg.base, ws.item_lb.as<float>() + sg.base,
+                           &ctrl->seg_count[si], sg.cap, &ctrl->seg_head[si]);
         a.G = sg.G;
-        a.thr = ws.thr.as<float>();
-        a.mu_keep = pl.mg.mu_keep;
-        a.mu_prune = pl.mg.mu_prune;
-        a.k = p.k;
-        a.kslots = pl.kslots;
-        a.slots = ws.slots.as<unsigned long long>();
-        a.eps_list = ws.eps_list.as<unsigned long long>();
-        a.eps_count = ws.eps_count.as<int>();
-        a.eps_cap = (int)pl.eps_cap;
-        a.stats = stats;
-        a.status = &ctrl->status;
+        a.cells_stat = STAT_DP_CELLS;
         const int occ = dp_max_blocks_per_sm(db->deff, sg.P, kind);
         launch_dp(a, db->deff, sg.P, kind, db->n_sm * std::max(occ, 1), st);
         ++launches;
     }
-    if (sev)
-        cudaEventRecord(sev->ev[3], st);
+    if (sev) {
+        cudaEventRecord(sev->seg[pl.segs.size()], st);
+        cudaEventRecord(sev->ev[5], st);
+    }
 
     FinArgs f{};
     f.nq = nq;
@@ -335,7 +433,6 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     f.rer_list = ws.rer_list.as<int2>();
     f.rer_count = &ctrl->rer_count;
     f.rer_cap = pl.rer_cap;
-    f.rer_scratch = ws.rer_scratch.as<double>();
     f.rer_row = pl.rer_row;
     f.db = db->data.as<float>();
     f.db_off_by_id = db->off_by_id.as<int64_t>();
@@ -353,7 +450,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     launch_finalize(f, st);
     launches += 3;
     if (sev)
-        cudaEventRecord(sev->ev[4], st);
+        cudaEventRecord(sev->ev[6], st);
     return launches;
 }
 
@@ -399,7 +496,7 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         if (!out_counts)
             return set_error(KNN_ERR_INVALID, "eps-NN needs out_counts");
     }
-    if (p.seed_mode < KNN_SEED_GREEDY || p.seed_mode > KNN_SEED_NONE)
+    if (p.seed_mode < KNN_SEED_GREEDY || p.seed_mode > KNN_SEED_LB)
         return set_error(KNN_ERR_INVALID, "unknown seed_mode");
     if (p.seed_mode == KNN_SEED_LEARNED && !db->enc)
         return set_error(KNN_ERR_INVALID, "learned seeding needs an attached encoder");
@@ -481,9 +578,14 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
     double stage_ms[4] = {0, 0, 0, 0};
     const bool profile = p.profile != 0 && !graph;
     StageEvents sev;
-    if (profile)
+    if (profile) {
         for (auto &ev : sev.ev)
             cudaEventCreate(&ev);
+        for (auto &ev : sev.seg)
+            cudaEventCreate(&ev);
+    }
+    db->seg_ms.clear();
+    db->seg_first_bucket.clear();
     for (int q0 = 0; q0 < n_queries; q0 += batch) {
         const int nq = std::min(batch, n_queries - q0);
         Plan pl;
@@ -551,13 +653,23 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         } else {
             launches += enqueue_batch(db, pl, p, qs, qso, oi, od, oc, st, profile ? &sev : nullptr);
             if (profile) {
-                e = cudaEventSynchronize(sev.ev[4]);
+                e = cudaEventSynchronize(sev.ev[6]);
                 if (e != cudaSuccess)
                     return cuda_error(e, "stage events");
-                for (int i = 0; i < 4; ++i) {
+                float t[6];
+                for (int i = 0; i < 6; ++i)
+                    cudaEventElapsedTime(&t[i], sev.ev[i], sev.ev[i + 1]);
+                stage_ms[0] += t[0] + t[2];  // seeding: greedy pre-pass, or seeds
+                stage_ms[1] += t[1] + t[3];  // envelopes, LB_Box stream, filter
+                stage_ms[2] += t[4];         // DP
+                stage_ms[3] += t[5];         // finalise
+                db->seg_ms.resize(pl.segs.size(), 0.0);
+                db->seg_first_bucket.resize(pl.segs.size());
+                for (size_t si = 0; si < pl.segs.size(); ++si) {
                     float ms = 0.f;
-                    cudaEventElapsedTime(&ms, sev.ev[i], sev.ev[i + 1]);
-                    stage_ms[i] += ms;
+                    cudaEventElapsedTime(&ms, sev.seg[si], sev.seg[si + 1]);
+                    db->seg_ms[si] += ms;
+                    db->seg_first_bucket[si] = pl.segs[si].b_begin;
                 }
             }
         }
@@ -588,15 +700,19 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
-    if (profile)
+    if (profile) {
         for (auto &ev : sev.ev)
             cudaEventDestroy(ev);
+        for (auto &ev : sev.seg)
+            cudaEventDestroy(ev);
+    }
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->pairs = (int64_t)hc.stats[STAT_PAIRS];
         stats->band_infeasible = (int64_t)hc.stats[STAT_INFEASIBLE];
         stats->ub_walks = (int64_t)hc.stats[STAT_UB_WALKS];
         stats->seeds = (int64_t)hc.stats[STAT_SEEDS];
+        stats->seed_cells = (int64_t)hc.stats[STAT_SEED_CELLS];
         stats->lb_pruned = (int64_t)hc.stats[STAT_LB_PRUNED];
         stats->lb_pruned_late = (int64_t)hc.stats[STAT_LB_PRUNED_LATE];
         stats->dp_calls = (int64_t)hc.stats[STAT_DP_CALLS];

@@ -181,12 +181,15 @@ def test_scan_tiny_config(kw, kind):
 
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("k,band", [(1, 0.05), (10, 0.05), (10, 0.1)])
-def test_scan_scale_shape(kw, kind, k, band):
+@pytest.mark.parametrize("seed", [0, 3])
+def test_scan_scale_shape(kw, kind, k, band, seed):
     """d=3 length 256 at reduced N: spans many warp tiles plus a ragged tail."""
     w = make_workload(n_series=3001, n_queries=12, d=3, length=256, n_classes=20, seed=1)
-    (ids, dist), _ = run_scan(kw, w, k=k, band=band, kind=kind)
+    (ids, dist), st = run_scan(kw, w, k=k, band=band, kind=kind, seed=seed)
     oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(band), kind=kind, k=k)
     check_knn(ids, dist, oids, odist, kind, k)
+    if seed == 3:
+        assert st["seeds"] == 12 * max(64, 4 * k)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
@@ -231,8 +234,9 @@ def test_seed_modes_and_graph_give_identical_results(kw):
     w = make_workload(n_series=2500, n_queries=8, d=3, length=96, n_classes=10, seed=8)
     for kind in (0, 1):
         base, _ = run_scan(kw, w, k=7, band=0.1, kind=kind, seed=0)
-        for kwargs in (dict(seed=2), dict(seed=0, use_graph=True), dict(seed=0, query_batch=3),
-                       dict(seed=0, host=True)):
+        for kwargs in (dict(seed=2), dict(seed=3), dict(seed=3, seed_count=5),
+                       dict(seed=3, use_graph=True), dict(seed=0, use_graph=True),
+                       dict(seed=0, query_batch=3), dict(seed=0, host=True)):
             other, _ = run_scan(kw, w, k=7, band=0.1, kind=kind, **kwargs)
             np.testing.assert_array_equal(base[0], other[0])
             np.testing.assert_array_equal(base[1], other[1])
@@ -314,3 +318,55 @@ def test_scan_simple_north_star_form(kw):
         ids, dist = kw.scan_simple(w.query(0), w.db, lens, d=3, band=0.1, k=5, distance=kind)
         oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(0.1), kind=kind, k=5)
         check_knn(ids[None], dist[None], oids, odist, kind, 5)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_every_dp_shape_gives_identical_results(kw, kind):
+    """The autotuner may pick any compiled shape: all must return the same."""
+    w = make_workload(n_series=1500, n_queries=6, d=3, length=128, n_classes=8, seed=15)
+    band, k = 0.1, 5
+    r = oracle.band_radius(128, 128, f32(band))
+    oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(band), kind=kind, k=k)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    shapes = []
+    for P in kw.dp_shapes(3):
+        G = 1
+        while G * P < r + 1:
+            G *= 2
+        for g in (G, 2 * G):
+            if g <= 32:
+                shapes.append((P, g))
+    assert len(shapes) >= 4
+    for seed in (0, 3):
+        for P, G in shapes:
+            db.set_dp_shape(kind, r, 128, P, G)
+            assert db.get_dp_shape(kind, r, 128) == (P, G)
+            ids, dist = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind, seed=seed)
+            check_knn(ids.cpu().numpy(), dist.cpu().numpy(), oids, odist, kind, k)
+    with pytest.raises(kw.KnnError):
+        db.set_dp_shape(kind, r, 128, 3, 32)          # P=3 is not compiled
+    with pytest.raises(kw.KnnError):
+        db.set_dp_shape(kind, r, 128, 2, 1)           # G*P < r+1
+    db.close()
+
+
+def test_autotune_and_cache(kw, tmp_path):
+    w = make_workload(n_series=3000, n_queries=16, d=3, length_range=(60, 200), n_classes=8,
+                      seed=16)
+    cache = str(tmp_path / "shapes.json")
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    base = db.scan(cuda(w.q), w.q_off, k=5, band=0.1, distance=0, seed=3)
+    db.autotune(cuda(w.q), w.q_off, k=5, band=0.1, distance=0, cache_path=cache)
+    tuned = db.scan(cuda(w.q), w.q_off, k=5, band=0.1, distance=0, seed=3)
+    assert (tuned[0] == base[0]).all() and (tuned[1] == base[1]).all()
+    import json
+    entries = json.load(open(cache))["dp_shapes"]
+    assert len(entries) == db.info()["n_buckets"]
+    assert all(e["P"] * e["G"] >= e["r"] + 1 for e in entries)
+    db.close()
+    # a fresh database reuses the cached shapes without re-timing
+    db2 = kw.KnnDB(cuda(w.db), w.db_off)
+    db2.autotune(cuda(w.q), w.q_off, k=5, band=0.1, distance=0, cache_path=cache)
+    e = entries[0]
+    assert db2.get_dp_shape(0, e["r"], e["n"]) == (e["P"], e["G"])
+    db2.close()
