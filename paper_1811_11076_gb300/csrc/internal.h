@@ -59,6 +59,7 @@ struct LbArgs {
     int64_t out_lb_stride;
     unsigned long long *stats; // [STAT_*]
     int *status;
+    int single_query_kernel;   // 1: always the warp-per-series kernel
 };
 void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();

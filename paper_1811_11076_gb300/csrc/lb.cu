@@ -269,11 +269,162 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-query LB_Box kernel: grid (x: blocks of 256 series, y: query tiles).
+//
+// One thread owns one series and QT queries: it loads a chunk of its series
+// once and bounds it against the QT query envelopes, which the CTA staged in
+// shared memory with one TMA bulk copy per array; when the series of a warp
+// have the same length every lane reads the same envelope address (a
+// broadcast).  So the database is read once per QT queries and each element
+// costs 4 FP32 operations per query (max, min, sub, fma).
+
+template <int D, int FORM, int QT>
+__global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
+{
+    constexpr int CH = chunk_floats(D);
+    constexpr int PPC = chunk_points(D);
+    constexpr int F4 = CH / 4;
+    extern __shared__ __align__(128) float4 env_s[];  // [QT][stride] lo, then [QT][stride] hi
+    __shared__ __align__(8) uint64_t bar;
+
+    const int q0 = blockIdx.y * QT;
+    const int nqt = min(QT, a.nq - q0);
+    const int lane = threadIdx.x & 31;
+    const int st4 = (int)(a.env_stride / 4);
+    const float4 *lo_s = env_s;
+    const float4 *hi_s = env_s + QT * st4;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(nqt * a.env_stride * 4);
+        mbar_expect_tx(&bar, 2u * bytes);
+        tma_bulk_g2s(env_s, a.env_lo + (int64_t)q0 * a.env_stride, bytes, &bar);
+        tma_bulk_g2s(env_s + QT * st4, a.env_hi + (int64_t)q0 * a.env_stride, bytes, &bar);
+    }
+    if (!mbar_wait0(&bar)) {
+        if (lane == 0)
+            atomicOr(a.status, KNN_DEV_TIMEOUT);
+        return;
+    }
+
+    int mq[QT];
+#pragma unroll
+    for (int j = 0; j < QT; ++j)
+        mq[j] = j < nqt ? a.q_len[q0 + j] : 1;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0;
+    const int nser = a.c_end - a.c_begin;
+    const int span = (nser + LB_THREADS - 1) / LB_THREADS * LB_THREADS;
+    for (int i = blockIdx.x * LB_THREADS + threadIdx.x; i < span; i += gridDim.x * LB_THREADS) {
+        const bool valid = i < nser;
+        const int c = a.c_begin + (valid ? i : 0);
+        const int n = valid ? a.db_len[c] : 0;
+        float acc[QT];
+#pragma unroll
+        for (int j = 0; j < QT; ++j)
+            acc[j] = 0.f;
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+        const int nch = (n + PPC - 1) / PPC;
+        for (int ch = 0; ch < nch; ++ch) {
+            float v[CH];
+#pragma unroll
+            for (int f = 0; f < F4; ++f) {
+                const float4 t = __ldg(x4 + ch * F4 + f);
+                v[4 * f] = t.x; v[4 * f + 1] = t.y; v[4 * f + 2] = t.z; v[4 * f + 3] = t.w;
+            }
+#pragma unroll
+            for (int j = 0; j < QT; ++j) {
+                float l[CH], u[CH];
+#pragma unroll
+                for (int f = 0; f < F4; ++f) {
+                    const float4 lv = lo_s[j * st4 + ch * F4 + f];
+                    const float4 uv = hi_s[j * st4 + ch * F4 + f];
+                    l[4 * f] = lv.x; l[4 * f + 1] = lv.y; l[4 * f + 2] = lv.z; l[4 * f + 3] = lv.w;
+                    u[4 * f] = uv.x; u[4 * f + 1] = uv.y; u[4 * f + 2] = uv.z; u[4 * f + 3] = uv.w;
+                }
+#pragma unroll
+                for (int p = 0; p < PPC; ++p) {
+                    float box = 0.f;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const float x = v[p * D + k];
+                        const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
+                        box = __fmaf_rn(e, e, box);
+                    }
+                    if (ch * PPC + p < n)
+                        acc[j] = FORM == 0 ? acc[j] + box : fmaxf(acc[j], box);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < QT; ++j) {
+            if (j >= nqt)
+                break;
+            const int qb = q0 + j;
+            const int r = band_radius(mq[j], n, a.band);
+            const bool feasible = valid && abs(mq[j] - n) <= r;
+            const float lb = feasible ? acc[j] : KNN_INF;
+            if (valid && a.out_lb)
+                a.out_lb[(int64_t)qb * a.out_lb_stride + c] = lb;
+            st_pairs += valid;
+            st_inf += valid && !feasible;
+            if (a.items) {
+                const float thr = ld_volatile_f32(a.thr + qb);
+                const bool keep = feasible && lb <= thr * a.mu_prune;
+                st_pruned += feasible && !keep;
+                const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
+                if (kb) {
+                    int base = 0;
+                    if (lane == 0)
+                        base = atomicAdd(a.n_items, __popc(kb));
+                    base = __shfl_sync(KNN_FULL_MASK, base, 0);
+                    if (keep) {
+                        const int64_t pos = (int64_t)base + __popc(kb & ((1u << lane) - 1u));
+                        if (pos < a.capacity) {
+                            a.items[pos] = make_int2(c, qb);
+                            a.item_lb[pos] = lb;
+                        } else {
+                            atomicOr(a.status, KNN_DEV_CAPACITY);
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_pairs += __shfl_xor_sync(KNN_FULL_MASK, st_pairs, o);
+        st_inf += __shfl_xor_sync(KNN_FULL_MASK, st_inf, o);
+        st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
+    }
+    if (lane == 0 && a.stats) {
+        atomicAdd(a.stats + STAT_PAIRS, st_pairs);
+        atomicAdd(a.stats + STAT_INFEASIBLE, st_inf);
+        atomicAdd(a.stats + STAT_LB_PRUNED, st_pruned);
+    }
+}
+
+template <int D, int QT>
+static void lb_attr_q()
+{
+    cudaFuncSetAttribute(lb_multi_kernel<D, 0, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(lb_multi_kernel<D, 1, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+}
+
 template <int D>
 static void lb_attr_d()
 {
     cudaFuncSetAttribute(lb_kernel<D, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(lb_kernel<D, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    lb_attr_q<D, 4>();
+    lb_attr_q<D, 8>();
+    lb_attr_q<D, 16>();
 }
 
 void lb_init_attributes()
@@ -282,9 +433,38 @@ void lb_init_attributes()
     lb_attr_d<6>(); lb_attr_d<7>(); lb_attr_d<8>(); lb_attr_d<16>();
 }
 
+template <int D, int QT>
+static void lb_multi_launch(const LbArgs &a, int form, int n_sm, cudaStream_t st)
+{
+    const size_t smem = (size_t)QT * a.env_stride * 4 * 2;
+    const int nser = a.c_end - a.c_begin;
+    const int qtiles = (a.nq + QT - 1) / QT;
+    int bx = (nser + LB_THREADS - 1) / LB_THREADS;
+    const int want = (n_sm * 8 + qtiles - 1) / qtiles;
+    bx = bx < want ? bx : want;
+    if (bx < 1)
+        bx = 1;
+    dim3 grid(bx, qtiles);
+    if (form == 0)
+        lb_multi_kernel<D, 0, QT><<<grid, LB_THREADS, smem, st>>>(a);
+    else
+        lb_multi_kernel<D, 1, QT><<<grid, LB_THREADS, smem, st>>>(a);
+}
+
 template <int D>
 static void lb_launch_d(const LbArgs &a, int form, int n_sm, cudaStream_t st)
 {
+    // several queries: the multi-query kernel with the largest tile whose
+    // envelopes fit in shared memory
+    const size_t per_q = (size_t)a.env_stride * 4 * 2;
+    if (a.nq >= 4 && !a.single_query_kernel) {
+        if (a.nq >= 16 && 16 * per_q <= 192 * 1024)
+            return lb_multi_launch<D, 16>(a, form, n_sm, st);
+        if (a.nq >= 8 && 8 * per_q <= 192 * 1024)
+            return lb_multi_launch<D, 8>(a, form, n_sm, st);
+        if (4 * per_q <= 192 * 1024)
+            return lb_multi_launch<D, 4>(a, form, n_sm, st);
+    }
     const size_t smem = (size_t)a.env_floats * 4 * 2;
     auto kern = form == 0 ? lb_kernel<D, 0> : lb_kernel<D, 1>;
     const int nser = a.c_end - a.c_begin;
