@@ -234,6 +234,31 @@ KNN_API knn_status knn_pairwise(const float *a, const int64_t *a_off, const floa
                                 int64_t n_pairs, int32_t d, float band, int32_t distance,
                                 float *out_f32, double *out_f64, void *stream);
 
+/* Same FP32 results as knn_pairwise's out_f32, for callers who cannot let
+ * the library allocate device memory (their memory belongs to their own
+ * allocator, or cudaMalloc/cudaFree, which may synchronise the device, are not
+ * acceptable where they call).  The paper has no counterpart: this is an
+ * interface for such callers.  Nothing is allocated: the scratch (repacked
+ * series, pair queue, results, counters) is one fixed array of about 9.4 MB
+ * inside the library, present on every device that loads it until exit.
+ * Limits: n_pairs <= 65536; 1 <= n_a, n_b <= 16384 series per set; after
+ * padding each series to whole chunks of lcm(d', 4) floats (d' = d, or 16
+ * for 9 <= d <= 16) at most 1,048,576 floats per set; max_len (an upper bound
+ * on every series length, used to choose the DP shape) <= 65536.  Larger
+ * inputs are rejected (KNN_ERR_INVALID for counts, KNN_ERR_CAPACITY for the
+ * padded sizes) and nothing is computed.  All pointers are device memory;
+ * a_off / b_off have n_a + 1 / n_b + 1 point offsets; out receives n_pairs
+ * floats.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make it before capturing
+ * any stream.  Every call shares the array and clears its counters; calls
+ * that overlap on the GPU race and must be serialised by the caller.  The
+ * call synchronises `stream` before returning. */
+KNN_API knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off, int64_t n_a,
+                                        const float *b, const int64_t *b_off, int64_t n_b,
+                                        const int64_t *pa, const int64_t *pb, int64_t n_pairs,
+                                        int32_t d, float band, int32_t max_len,
+                                        int32_t distance, float *out, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Diagnostics                                                              */
 

@@ -37,7 +37,7 @@ STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA"
 EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
-           "knn_dp_shapes")
+           "knn_dp_shapes", "knn_pairwise_noalloc")
 
 
 class KnnError(RuntimeError):
@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
     L.knn_set_dp_shape.argtypes = [vp] + [C.c_int32] * 5
     L.knn_get_dp_shape.argtypes = [vp] + [C.c_int32] * 3 + [C.POINTER(C.c_int32)] * 2
     L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
+    L.knn_pairwise_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp, C.c_int64,
+                                       C.c_int32, C.c_float, C.c_int32, C.c_int32, vp, vp]
     for f in EXPORTS:
         if f not in ("knn_status_string", "knn_last_error", "knn_version"):
             getattr(L, f).restype = C.c_int
