@@ -207,7 +207,10 @@ def run_gpu(args):
     shapes = {}
     r = int(np.float64(np.float32(BAND)) * LENGTH)
     for kind in kinds:
-        if not args.no_autotune:
+        if args.shape:
+            P, G = (int(v) for v in args.shape.split(","))
+            db.set_dp_shape(kind, r, LENGTH, P, G)
+        elif not args.no_autotune:
             nt = min(nq, 128)
             db.autotune(q_dev[: int(q_off[nt])], q_off_t[: nt + 1], k=K, band=BAND, distance=kind,
                         seed=seed_mode)
@@ -362,6 +365,7 @@ def main():
                     help="queries per GPU (smaller values only for profiling captures)")
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--shape", default="", help="P,G: fix the DP shape instead of tuning it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
