@@ -216,6 +216,31 @@ extern "C" knn_status knn_autotune(knn_db *db, const float *queries, const int64
     for (auto &kv : cached)
         if (!db->tuned.count(kv.first))
             db->tuned[kv.first] = kv.second;
+    // queries per LB_Box pass: time the LB stage with each tile
+    if (n_queries >= 8) {
+        double best_lb = 1e300;
+        int best_q = 0;
+        for (int qt : {16, 8, 4}) {
+            db->lb_qtile[p.distance] = qt;
+            knn_stats st{};
+            double tot = 0.0;
+            for (int rep = 0; rep < 2 && !s; ++rep) {
+                s = knn_scan(db, queries, q_offsets, n_queries, &p, ids.data(), dist.data(),
+                             nullptr, &st, stream);
+                if (rep == 1)
+                    tot = st.ms_lb;
+            }
+            if (s)
+                break;
+            if (tot < best_lb) {
+                best_lb = tot;
+                best_q = qt;
+            }
+        }
+        db->lb_qtile[p.distance] = best_q;
+        if (s)
+            return s;
+    }
     if (cache_path)
         save_cache(cache_path, dev, db->deff, db->tuned, ms);
     return KNN_OK;

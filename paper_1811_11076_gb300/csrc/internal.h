@@ -60,6 +60,7 @@ struct LbArgs {
     unsigned long long *stats; // [STAT_*]
     int *status;
     int single_query_kernel;   // 1: always the warp-per-series kernel
+    int qtile;                 // queries per CTA of the multi-query kernel (0: largest fitting)
 };
 void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();

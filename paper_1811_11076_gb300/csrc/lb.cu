@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
         const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
         const int nch = (n + PPC - 1) / PPC;
         for (int ch = 0; ch < nch; ++ch) {
+            const bool full = (ch + 1) * PPC <= n;
             float v[CH];
 #pragma unroll
             for (int f = 0; f < F4; ++f) {
@@ -346,17 +347,42 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
                     l[4 * f] = lv.x; l[4 * f + 1] = lv.y; l[4 * f + 2] = lv.z; l[4 * f + 3] = lv.w;
                     u[4 * f] = uv.x; u[4 * f + 1] = uv.y; u[4 * f + 2] = uv.z; u[4 * f + 3] = uv.w;
                 }
+                if (full) {
+                    // whole chunk inside the series: no per-point test
+                    if (FORM == 0) {
+                        float sacc = acc[j];
 #pragma unroll
-                for (int p = 0; p < PPC; ++p) {
-                    float box = 0.f;
+                        for (int e2 = 0; e2 < CH; ++e2) {
+                            const float e = v[e2] - fminf(fmaxf(v[e2], l[e2]), u[e2]);
+                            sacc = __fmaf_rn(e, e, sacc);
+                        }
+                        acc[j] = sacc;
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < D; ++k) {
-                        const float x = v[p * D + k];
-                        const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
-                        box = __fmaf_rn(e, e, box);
+                        for (int p = 0; p < PPC; ++p) {
+                            float box = 0.f;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                const float x = v[p * D + k];
+                                const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
+                                box = __fmaf_rn(e, e, box);
+                            }
+                            acc[j] = fmaxf(acc[j], box);
+                        }
                     }
-                    if (ch * PPC + p < n)
-                        acc[j] = FORM == 0 ? acc[j] + box : fmaxf(acc[j], box);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < PPC; ++p) {
+                        float box = 0.f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            const float x = v[p * D + k];
+                            const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
+                            box = __fmaf_rn(e, e, box);
+                        }
+                        if (ch * PPC + p < n)
+                            acc[j] = FORM == 0 ? acc[j] + box : fmaxf(acc[j], box);
+                    }
                 }
             }
         }
@@ -458,9 +484,10 @@ static void lb_launch_d(const LbArgs &a, int form, int n_sm, cudaStream_t st)
     // envelopes fit in shared memory
     const size_t per_q = (size_t)a.env_stride * 4 * 2;
     if (a.nq >= 4 && !a.single_query_kernel) {
-        if (a.nq >= 16 && 16 * per_q <= 192 * 1024)
+        const int want = a.qtile > 0 ? a.qtile : 16;
+        if (want >= 16 && a.nq >= 16 && 16 * per_q <= 192 * 1024)
             return lb_multi_launch<D, 16>(a, form, n_sm, st);
-        if (a.nq >= 8 && 8 * per_q <= 192 * 1024)
+        if (want >= 8 && a.nq >= 8 && 8 * per_q <= 192 * 1024)
             return lb_multi_launch<D, 8>(a, form, n_sm, st);
         if (4 * per_q <= 192 * 1024)
             return lb_multi_launch<D, 4>(a, form, n_sm, st);

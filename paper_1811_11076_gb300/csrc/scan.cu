@@ -326,6 +326,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         l.env_floats = (int)((int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
         l.thr = ws.thr.as<float>();
         l.mu_prune = pl.mg.mu_prune;
+        l.qtile = db->lb_qtile[kind];
         if (pl.seeded) {
             l.out_lb = ws.lb_all.as<float>();
             l.out_lb_stride = db->N;
