@@ -260,6 +260,65 @@ KNN_API knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off, in
                                         int32_t distance, float *out, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Learned proposal: a 1-D convolutional encoder (no counterpart in the     */
+/* paper; it generalises the upper-bound pre-pass of Section 4.3).  Three   */
+/* convolutions (kernel 5, 64 channels, ReLU), a mean over positions and a  */
+/* linear layer map a series to a 64-d embedding; ||e_a - e_b||^2 predicts  */
+/* the distance.  Convolutions and their gradients run on BF16 tensor cores */
+/* with FP32 accumulation; FP32 master weights, Adam.  The encoder only     */
+/* orders the work: scan results never depend on it.                        */
+
+typedef struct {
+    int32_t epochs;        /* passes over the training pairs                      */
+    int32_t batch_pairs;   /* pairs per optimiser step                            */
+    float lr;              /* Adam learning rate                                  */
+    int32_t distance;      /* knn_distance of the targets                         */
+    float band;            /* band of the target distances                        */
+    uint64_t seed;         /* pair sampling and shuffling                         */
+} knn_train_params;
+
+typedef struct {
+    double first_loss;     /* loss of the first step                              */
+    double final_loss;     /* mean loss of the last epoch                         */
+    double ms;             /* wall time on the stream                             */
+    int64_t pairs;         /* training pairs with a finite distance               */
+    int64_t steps;         /* optimiser steps                                     */
+} knn_train_stats;
+
+/* Number of parameters (FP32) of the encoder. */
+KNN_API int32_t knn_encoder_num_params(void);
+/* New encoder for d-dimensional series (1 <= d <= 16), He-normal weights. */
+KNN_API knn_status knn_encoder_create(int32_t d, uint64_t seed, knn_encoder **out);
+KNN_API knn_status knn_encoder_destroy(knn_encoder *enc);
+/* Train on n_pairs random pairs of database series; the target of a pair is
+ * its banded distance computed by the scan's DP (DTW divided by the longer
+ * length, or DK^2); loss (||e_a - e_b||^2 - target)^2. */
+KNN_API knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_pairs,
+                                     const knn_train_params *params, knn_train_stats *stats,
+                                     void *stream);
+/* Embeddings [n][64] (FP32, device) of n series (device, point offsets). */
+KNN_API knn_status knn_encoder_embed(knn_encoder *enc, const float *series,
+                                     const int64_t *offsets, int64_t n, float *out, void *stream);
+/* Embed every database series (BF16, kept by the database) so that scans
+ * with seed_mode = KNN_SEED_LEARNED can rank series by predicted distance. */
+KNN_API knn_status knn_encoder_attach(knn_db *db, knn_encoder *enc, void *stream);
+/* Read (get) and/or replace (set) the FP32 parameters, host arrays of
+ * knn_encoder_num_params() floats in the layout W1 [5][16][64], b1, W2
+ * [5][64][64], b2, W3 [5][64][64], b3, Wl [64][64] (in x out), bl. */
+KNN_API knn_status knn_encoder_params(knn_encoder *enc, float *get, const float *set);
+/* Mean loss and its gradient (host, knn_encoder_num_params() floats) for
+ * pairs (pa[i], pb[i]) of n_series series (device, point offsets) with
+ * targets (host or device). */
+KNN_API knn_status knn_encoder_loss_grad(knn_encoder *enc, const float *series,
+                                         const int64_t *offsets, int64_t n_series,
+                                         const int64_t *pa, const int64_t *pb,
+                                         const float *targets, int64_t n_pairs, float *loss,
+                                         float *grad, void *stream);
+/* Checkpoint: a JSON header line, then FP32 parameters and Adam moments. */
+KNN_API knn_status knn_encoder_save(const knn_encoder *enc, const char *path);
+KNN_API knn_status knn_encoder_load(const char *path, knn_encoder **out);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics                                                              */
 
 KNN_API const char *knn_status_string(knn_status s);

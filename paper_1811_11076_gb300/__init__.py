@@ -29,6 +29,7 @@ SEED_GREEDY = 0
 SEED_LEARNED = 1
 SEED_NONE = 2
 SEED_LB = 3
+SEED_LEARNED_ = SEED_LEARNED
 
 STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA",
           4: "KNN_ERR_TIMEOUT", 5: "KNN_ERR_CAPACITY", 6: "KNN_ERR_UNSUPPORTED"}
@@ -37,7 +38,9 @@ STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA"
 EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
-           "knn_dp_shapes", "knn_pairwise_noalloc")
+           "knn_dp_shapes", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
+           "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach",
+           "knn_encoder_params", "knn_encoder_loss_grad", "knn_encoder_save", "knn_encoder_load")
 
 
 class KnnError(RuntimeError):
@@ -51,6 +54,19 @@ class Params(C.Structure):
                 ("distance", C.c_int32), ("seed_mode", C.c_int32), ("seed_count", C.c_int32),
                 ("query_batch", C.c_int32), ("use_graph", C.c_int32),
                 ("eps_capacity", C.c_int64), ("profile", C.c_int32), ("reserved", C.c_int32)]
+
+
+class TrainParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch_pairs", C.c_int32), ("lr", C.c_float),
+                ("distance", C.c_int32), ("band", C.c_float), ("seed", C.c_uint64)]
+
+
+class TrainStats(C.Structure):
+    _fields_ = [("first_loss", C.c_double), ("final_loss", C.c_double), ("ms", C.c_double),
+                ("pairs", C.c_int64), ("steps", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Stats(C.Structure):
@@ -98,8 +114,21 @@ def lib() -> C.CDLL:
     L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
     L.knn_pairwise_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp, C.c_int64,
                                        C.c_int32, C.c_float, C.c_int32, C.c_int32, vp, vp]
+    L.knn_encoder_num_params.restype = C.c_int32
+    L.knn_encoder_create.argtypes = [C.c_int32, C.c_uint64, C.POINTER(vp)]
+    L.knn_encoder_destroy.argtypes = [vp]
+    L.knn_encoder_train.argtypes = [vp, vp, C.c_int64, C.POINTER(TrainParams),
+                                    C.POINTER(TrainStats), vp]
+    L.knn_encoder_embed.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
+    L.knn_encoder_attach.argtypes = [vp, vp, vp]
+    L.knn_encoder_params.argtypes = [vp, vp, vp]
+    L.knn_encoder_loss_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int64,
+                                        C.POINTER(C.c_float), vp, vp]
+    L.knn_encoder_save.argtypes = [vp, C.c_char_p]
+    L.knn_encoder_load.argtypes = [C.c_char_p, C.POINTER(vp)]
     for f in EXPORTS:
-        if f not in ("knn_status_string", "knn_last_error", "knn_version"):
+        if f not in ("knn_status_string", "knn_last_error", "knn_version",
+                     "knn_encoder_num_params"):
             getattr(L, f).restype = C.c_int
     L.knn_status_string.restype = C.c_char_p
     L.knn_status_string.argtypes = [C.c_int]
@@ -256,6 +285,91 @@ class KnnDB:
         _check(lib().knn_greedy_ub(self._h, _ptr(query), int(query.shape[0]), band, form,
                                    _ptr(out), _stream(stream)))
         return out
+
+
+class Encoder:
+    """The learned proposal's 1-D convolutional encoder (knn_encoder)."""
+
+    def __init__(self, d: int = 3, seed: int = 0, _handle=None):
+        if _handle is None:
+            h = C.c_void_p()
+            _check(lib().knn_encoder_create(d, seed, C.byref(h)))
+            _handle = h
+        self._h = _handle
+        self.d = d
+
+    @staticmethod
+    def num_params() -> int:
+        return int(lib().knn_encoder_num_params())
+
+    @classmethod
+    def load(cls, path: str) -> "Encoder":
+        h = C.c_void_p()
+        _check(lib().knn_encoder_load(path.encode(), C.byref(h)))
+        enc = cls(_handle=h)
+        enc.d = -1
+        return enc
+
+    def save(self, path: str):
+        _check(lib().knn_encoder_save(self._h, path.encode()))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().knn_encoder_params(self._h, out.ctypes.data, None))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.shape[0] == self.num_params()
+        _check(lib().knn_encoder_params(self._h, None, flat.ctypes.data))
+
+    def train(self, db: "KnnDB", n_pairs: int, *, epochs: int = 4, batch_pairs: int = 2048,
+              lr: float = 1e-3, distance: int = DTW, band: float = 0.1, seed: int = 0,
+              stream=None) -> dict:
+        tp = TrainParams(epochs=epochs, batch_pairs=batch_pairs, lr=lr, distance=distance,
+                         band=band, seed=seed)
+        st = TrainStats()
+        _check(lib().knn_encoder_train(self._h, db.handle, n_pairs, C.byref(tp), C.byref(st),
+                                       _stream(stream)))
+        return st.as_dict()
+
+    def embed(self, series, offsets, stream=None):
+        import torch
+        series = _f32(series)
+        offsets = _i64(offsets)
+        n = int(offsets.shape[0] - 1)
+        out = torch.empty((n, 64), dtype=torch.float32, device="cuda")
+        _check(lib().knn_encoder_embed(self._h, _ptr(series), _ptr(offsets), n, _ptr(out),
+                                       _stream(stream)))
+        return out
+
+    def attach(self, db: "KnnDB", stream=None):
+        _check(lib().knn_encoder_attach(db.handle, self._h, _stream(stream)))
+        db._encoder = self  # keep alive while attached
+
+    def loss_grad(self, series, offsets, pa, pb, targets, stream=None):
+        series = _f32(series)
+        offsets = _i64(offsets)
+        pa, pb = _i64(pa), _i64(pb)
+        targets = np.ascontiguousarray(targets, dtype=np.float32)
+        loss = C.c_float()
+        grad = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().knn_encoder_loss_grad(self._h, _ptr(series), _ptr(offsets),
+                                           int(offsets.shape[0] - 1), _ptr(pa), _ptr(pb),
+                                           targets.ctypes.data, int(pa.shape[0]),
+                                           C.byref(loss), grad.ctypes.data, _stream(stream)))
+        return loss.value, grad
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().knn_encoder_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dp_shapes(d: int) -> list[int]:

@@ -53,7 +53,7 @@ struct Workspace {
     DevBuf fin_valid, fin_vals, rer_list, rer_scratch;
     DevBuf out_ids, out_dist, out_counts;
     DevBuf skip;
-    DevBuf seed_items, seed_lb, scores, sel, lb_all;
+    DevBuf seed_items, seed_lb, scores, sel, lb_all, qemb, qnorm;
     uint64_t generation = 0;            // bumped whenever a buffer moves
 };
 
@@ -91,6 +91,10 @@ struct DpChoice {
 struct knn_db;
 namespace knn {
 DpChoice dp_choice(knn_db *db, int kind, int r, int n);
+knn_status enc_work(knn_encoder *enc, int B, int L);
+knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, const int *q_len,
+                           int nq, int max_m, void *qemb, float *qnorm, float *scores,
+                           cudaStream_t st);
 }
 
 struct knn_db {
@@ -103,7 +107,8 @@ struct knn_db {
     std::vector<knn::Bucket> buckets;
     knn::Workspace ws;
     knn_encoder *enc = nullptr;
-    knn::DevBuf emb;                      // [N][64] bf16 embeddings (caller id order)
+    knn::DevBuf emb;                      // [N][64] bf16 embeddings (bucket order)
+    knn::DevBuf emb_norm;                 // [N] squared norms of the bf16 embeddings
     std::map<knn::GraphKey, cudaGraphExec_t> graphs;
     cudaStream_t cap_stream = nullptr;    // private stream used only to capture graphs
     std::map<std::tuple<int, int, int>, knn::DpChoice> tuned;  // (kind, r, n) -> config

@@ -36,6 +36,7 @@ struct Plan {
     float eps_int = 0.f;
     int rer_row = 0, rer_cap = 0;
     bool seeded = false;
+    bool learned = false;       // seeds ranked by the encoder instead of LB_Box
     int S = 0;                  // seeds per query
     DpChoice seed_dp{};
 };
@@ -148,6 +149,7 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
         return set_error(KNN_ERR_UNSUPPORTED, "band too wide for FP64 re-scoring (r > 4000)");
     pl.rer_cap = 1024 + 8 * nq;
     pl.seeded = p.k > 0 && (p.seed_mode == KNN_SEED_LB || p.seed_mode == KNN_SEED_LEARNED);
+    pl.learned = pl.seeded && p.seed_mode == KNN_SEED_LEARNED;
     if (pl.seeded) {
         pl.S = p.seed_count > 0 ? p.seed_count : std::max(64, 4 * p.k);
         pl.S = std::max(pl.S, p.k);
@@ -158,6 +160,8 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
     }
     return KNN_OK;
 }
+
+bool p_learned(const Plan &pl) { return pl.learned; }
 
 knn_status size_workspace(knn_db *db, const Plan &pl)
 {
@@ -186,6 +190,13 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(out_ids, sizeof(int64_t) * nq * pl.width);
     G_(out_dist, sizeof(float) * nq * pl.width);
     G_(out_counts, sizeof(int64_t) * nq);
+    if (pl.seeded && p_learned(pl)) {
+        G_(scores, sizeof(float) * nq * (size_t)db->N);
+        G_(qemb, sizeof(uint16_t) * nq * 64);
+        G_(qnorm, sizeof(float) * nq);
+        if ((s = enc_work(db->enc, nq, pl.max_m)))
+            return s;
+    }
     if (pl.seeded) {
         G_(lb_all, sizeof(float) * nq * (size_t)db->N);
         G_(seed_items, sizeof(int2) * nq * (size_t)pl.S);
@@ -345,9 +356,17 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         cudaEventRecord(sev->ev[2], st);
 
     if (pl.seeded) {
-        // seeds: the S series of lowest LB_Box per query, scored exactly first
+        // seeds: the S series of lowest LB_Box (or predicted distance) per
+        // query, scored exactly first
         SelArgs sa{};
         sa.score = ws.lb_all.as<float>();
+        if (pl.learned) {
+            enc_scan_scores(db, ws.qbuf.as<float>(), ws.q_off.as<int64_t>(), ws.q_len.as<int>(),
+                            nq, pl.max_m, ws.qemb.p, ws.qnorm.as<float>(), ws.scores.as<float>(),
+                            st);
+            sa.score = ws.scores.as<float>();
+            launches += 7;
+        }
         sa.score_stride = db->N;
         sa.lb_all = ws.lb_all.as<float>();
         sa.lb_stride = db->N;
@@ -501,6 +520,8 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         return set_error(KNN_ERR_INVALID, "unknown seed_mode");
     if (p.seed_mode == KNN_SEED_LEARNED && !db->enc)
         return set_error(KNN_ERR_INVALID, "learned seeding needs an attached encoder");
+    if (p.seed_mode == KNN_SEED_LEARNED && p.k == 0)
+        return set_error(KNN_ERR_INVALID, "learned seeding applies to k-NN");
     cudaStream_t st = (cudaStream_t)stream;
     cudaSetDevice(db->dev);
 

@@ -1,0 +1,104 @@
+"""The learned proposal on the GPU: encoder gradients against the FP64
+reference on the same BF16-rounded weights and inputs, training, exactness of
+the learned scan, and what the trained network gains."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import encoder as oenc
+from synthdata import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_11076_gb300 as kw
+    from paper_1811_11076_gb300 import build
+    build.build()
+    kw.lib()
+    return kw
+
+
+def cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_num_params(kw):
+    assert kw.Encoder.num_params() == oenc.N_PARAMS
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_gradients_match_fp64_reference(kw, d):
+    w = make_workload(n_series=14, n_queries=0, d=d, length_range=(20, 70), n_classes=3, seed=d)
+    series = [w.series(i) for i in range(14)]
+    rng = np.random.default_rng(d)
+    pa = rng.integers(0, 14, 10)
+    pb = (pa + 1 + rng.integers(0, 13, 10)) % 14
+    targets = rng.uniform(0.5, 3.0, 10).astype(np.float32)
+    flat = oenc.init_params(d, seed=7).astype(np.float32)
+    flat[-64:] = rng.standard_normal(64).astype(np.float32) * 0.1
+    enc = kw.Encoder(d)
+    enc.set_params(flat)
+    loss, grad = enc.loss_grad(cuda(w.db), w.db_off, pa, pb, targets)
+    eloss, egrad = oenc.loss_and_grad(flat.astype(np.float64), series, pa, pb, targets, bf16=True)
+    assert loss == pytest.approx(eloss, rel=5e-3)
+    p = oenc.unflatten(grad.astype(np.float64))
+    e = oenc.unflatten(egrad)
+    for name, _ in oenc.SHAPES:
+        assert rel_err(p[name], e[name]) < 3e-2, (name, rel_err(p[name], e[name]))
+    # the embedding itself
+    emb = enc.embed(cuda(w.db), cuda(w.db_off)).cpu().numpy()
+    eemb, _ = oenc.forward(flat.astype(np.float64), series, bf16=True)
+    assert rel_err(emb, eemb) < 1e-2
+    enc.close()
+
+
+def test_save_load_roundtrip(kw, tmp_path):
+    enc = kw.Encoder(3, seed=5)
+    path = str(tmp_path / "enc.bin")
+    enc.save(path)
+    enc2 = kw.Encoder.load(path)
+    np.testing.assert_array_equal(enc.params(), enc2.params())
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_training_and_learned_scan(kw, kind):
+    """Training lowers the loss; the learned scan equals the oracle; and the
+    trained encoder needs fewer exact programs than an untrained one."""
+    w = make_workload(n_series=4000, n_queries=24, d=3, length=96, n_classes=10, seed=21)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    band, k = 0.1, 5
+    oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=float(np.float32(band)),
+                             kind=kind, k=k)
+
+    def scan(enc):
+        enc.attach(db)
+        ids, dist, st = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind,
+                                seed=kw.SEED_LEARNED, seed_count=32, stats=True)
+        ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+        for q in range(w.n_queries):
+            assert list(ids[q]) == list(oids[q])
+            np.testing.assert_allclose(dist[q], odist[q], rtol=1e-5 if kind == 0 else 1e-6)
+        return st
+
+    untrained = kw.Encoder(3, seed=1)
+    st0 = scan(untrained)
+    trained = kw.Encoder(3, seed=1)
+    tr = trained.train(db, 20000, epochs=6, batch_pairs=512, lr=2e-3, distance=kind, band=band)
+    assert tr["final_loss"] < 0.5 * tr["first_loss"], tr
+    st1 = scan(trained)
+    assert st1["seeds"] == st0["seeds"] == 24 * 32
+    # what the trained network gains: fewer exact programs after the seeds
+    assert st1["dp_calls"] < st0["dp_calls"], (st0, st1)
+    db.close()
