@@ -91,7 +91,11 @@ struct SelArgs {
     const float *score;        // [nq][score_stride] ranking score per series (bucket order)
     int64_t score_stride;
     float *lb_all;             // [nq][lb_stride] LB_Box per series; seeds are set to -1
+                               // (nullable: feasibility from the lengths, seed bound 0)
     int64_t lb_stride;
+    const int *q_len;          // with lb_all == nullptr: lengths for the band test
+    const int *db_len;
+    float band;
     int n;                     // series
     int c_base;                // index of score[0] in bucket order
     int nq;

@@ -313,9 +313,14 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
     }
 
     int mq[QT];
+    float lim[QT];  // filter mode: a series is done once every bound exceeds its limit
 #pragma unroll
-    for (int j = 0; j < QT; ++j)
+    for (int j = 0; j < QT; ++j) {
         mq[j] = j < nqt ? a.q_len[q0 + j] : 1;
+        lim[j] = (a.items && j < nqt) ? ld_volatile_f32(a.thr + q0 + j) * a.mu_prune : KNN_INF;
+        if (j >= nqt)
+            lim[j] = -1.f;
+    }
     unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0;
     const int nser = a.c_end - a.c_begin;
     const int span = (nser + LB_THREADS - 1) / LB_THREADS * LB_THREADS;
@@ -330,6 +335,17 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
         const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
         const int nch = (n + PPC - 1) / PPC;
         for (int ch = 0; ch < nch; ++ch) {
+            if (a.items && (ch & 3) == 0) {
+                // early abandoning of the bound (Section 4): partial sums and
+                // maxima only grow, so once all exceed their limits the series
+                // is pruned for every query of the tile
+                bool all_over = true;
+#pragma unroll
+                for (int j = 0; j < QT; ++j)
+                    all_over &= acc[j] > lim[j];
+                if (all_over)
+                    break;
+            }
             const bool full = (ch + 1) * PPC <= n;
             float v[CH];
 #pragma unroll
@@ -399,8 +415,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
             st_pairs += valid;
             st_inf += valid && !feasible;
             if (a.items) {
-                const float thr = ld_volatile_f32(a.thr + qb);
-                const bool keep = feasible && lb <= thr * a.mu_prune;
+                const bool keep = feasible && lb <= lim[j];
                 st_pruned += feasible && !keep;
                 const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
                 if (kb) {

@@ -197,8 +197,10 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
         if ((s = enc_work(db->enc, nq, pl.max_m)))
             return s;
     }
-    if (pl.seeded) {
+    if (pl.seeded && !pl.learned) {
         G_(lb_all, sizeof(float) * nq * (size_t)db->N);
+    }
+    if (pl.seeded) {
         G_(seed_items, sizeof(int2) * nq * (size_t)pl.S);
         G_(seed_lb, sizeof(float) * nq * (size_t)pl.S);
     }
@@ -301,10 +303,42 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
             ++launches;
         }
     }
+
+    // learned proposal: seeds from the encoder's ranking, scored exactly
+    // before the LB_Box stream, so that the stream prunes (and abandons)
+    // against the seeded threshold directly
+    if (pl.learned) {
+        enc_scan_scores(db, ws.qbuf.as<float>(), ws.q_off.as<int64_t>(), ws.q_len.as<int>(), nq,
+                        pl.max_m, ws.qemb.p, ws.qnorm.as<float>(), ws.scores.as<float>(), st);
+        SelArgs sa{};
+        sa.score = ws.scores.as<float>();
+        sa.score_stride = db->N;
+        sa.q_len = ws.q_len.as<int>();
+        sa.db_len = db->len.as<int>();
+        sa.band = p.band;
+        sa.n = db->N;
+        sa.nq = nq;
+        sa.S = pl.S;
+        sa.seed_items = ws.seed_items.as<int2>();
+        sa.seed_lb = ws.seed_lb.as<float>();
+        sa.n_seed = &ctrl->n_seed;
+        sa.seed_cap = nq * pl.S;
+        sa.stats = stats;
+        sa.status = &ctrl->status;
+        launch_select(sa, st);
+        DpArgs a = dp_args(db, pl, p, ws.seed_items.as<int2>(), ws.seed_lb.as<float>(),
+                           &ctrl->n_seed, (int64_t)nq * pl.S, &ctrl->seed_head);
+        a.G = pl.seed_dp.G;
+        a.cells_stat = STAT_SEED_CELLS;
+        const int occ = dp_max_blocks_per_sm(db->deff, pl.seed_dp.P, kind);
+        launch_dp(a, db->deff, pl.seed_dp.P, kind, db->n_sm * std::max(occ, 1), st);
+        launches += 9;
+    }
     if (sev)
         cudaEventRecord(sev->ev[1], st);
 
-    // envelope + LB_Box stream per bucket (seeded: store every bound)
+    // envelope + LB_Box stream per bucket (LB-ordered seeding: store every bound)
+    const bool store = pl.seeded && !pl.learned;
     for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
         const Bucket &b = db->buckets[bi];
         const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];
@@ -338,7 +372,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         l.thr = ws.thr.as<float>();
         l.mu_prune = pl.mg.mu_prune;
         l.qtile = db->lb_qtile[kind];
-        if (pl.seeded) {
+        if (store) {
             l.out_lb = ws.lb_all.as<float>();
             l.out_lb_stride = db->N;
         } else {
@@ -355,18 +389,10 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     if (sev)
         cudaEventRecord(sev->ev[2], st);
 
-    if (pl.seeded) {
-        // seeds: the S series of lowest LB_Box (or predicted distance) per
-        // query, scored exactly first
+    if (store) {
+        // seeds: the S series of lowest LB_Box per query, scored exactly first
         SelArgs sa{};
         sa.score = ws.lb_all.as<float>();
-        if (pl.learned) {
-            enc_scan_scores(db, ws.qbuf.as<float>(), ws.q_off.as<int64_t>(), ws.q_len.as<int>(),
-                            nq, pl.max_m, ws.qemb.p, ws.qnorm.as<float>(), ws.scores.as<float>(),
-                            st);
-            sa.score = ws.scores.as<float>();
-            launches += 7;
-        }
         sa.score_stride = db->N;
         sa.lb_all = ws.lb_all.as<float>();
         sa.lb_stride = db->N;
@@ -391,7 +417,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     }
     if (sev)
         cudaEventRecord(sev->ev[3], st);
-    if (pl.seeded) {
+    if (store) {
         for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
             const Bucket &b = db->buckets[bi];
             const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];

@@ -24,7 +24,15 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
     __shared__ int s_bin, s_before, s_taken, s_count;
     const int q = blockIdx.x;
     const float *score = a.score + (int64_t)q * a.score_stride;
-    float *lb = a.lb_all + (int64_t)q * a.lb_stride;
+    float *lb = a.lb_all ? a.lb_all + (int64_t)q * a.lb_stride : nullptr;
+    const int m = a.lb_all ? 0 : a.q_len[q];
+    // a series can be a seed if its end cell is inside the band
+    auto feasible = [&](int c) -> bool {
+        if (lb)
+            return lb[c] < KNN_INF;
+        const int n = a.db_len[a.c_base + c];
+        return abs(m - n) <= band_radius(m, n, a.band);
+    };
     for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x)
         hist[i] = 0;
     if (threadIdx.x == 0) {
@@ -34,7 +42,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
     __syncthreads();
     for (int c = threadIdx.x; c < a.n; c += blockDim.x) {
         const float s = score[c];
-        if (s < KNN_INF && lb[c] < KNN_INF)
+        if (s < KNN_INF && feasible(c))
             atomicAdd(&hist[__float_as_uint(fmaxf(s, 0.f)) >> 20], 1u);
     }
     __syncthreads();
@@ -53,7 +61,7 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
     const int bin = s_bin, quota = a.S - s_before;
     for (int c = threadIdx.x; c < a.n; c += blockDim.x) {
         const float s = score[c];
-        if (!(s < KNN_INF) || !(lb[c] < KNN_INF))
+        if (!(s < KNN_INF) || !feasible(c))
             continue;
         const int sb = (int)(__float_as_uint(fmaxf(s, 0.f)) >> 20);
         bool take = sb < bin;
@@ -63,8 +71,9 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
             const int pos = atomicAdd(a.n_seed, 1);
             if (pos < a.seed_cap) {
                 a.seed_items[pos] = make_int2(a.c_base + c, q);
-                a.seed_lb[pos] = lb[c];
-                lb[c] = -1.f;  // scored as a seed; the filter skips it
+                a.seed_lb[pos] = lb ? lb[c] : 0.f;
+                if (lb)
+                    lb[c] = -1.f;  // scored as a seed; the filter skips it
                 atomicAdd(&s_count, 1);
             } else {
                 atomicOr(a.status, KNN_DEV_CAPACITY);

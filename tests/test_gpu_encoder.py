@@ -55,8 +55,12 @@ def test_gradients_match_fp64_reference(kw, d):
     assert loss == pytest.approx(eloss, rel=5e-3)
     p = oenc.unflatten(grad.astype(np.float64))
     e = oenc.unflatten(egrad)
+    scale = np.linalg.norm(egrad)
     for name, _ in oenc.SHAPES:
-        assert rel_err(p[name], e[name]) < 3e-2, (name, rel_err(p[name], e[name]))
+        # relative to the tensor, or to 1e-4 of the whole gradient where the
+        # exact tensor vanishes (the output bias: pair terms cancel exactly)
+        err = np.linalg.norm(p[name] - e[name]) / max(np.linalg.norm(e[name]), 1e-4 * scale)
+        assert err < 3e-2, (name, err)
     # the embedding itself
     emb = enc.embed(cuda(w.db), cuda(w.db_off)).cpu().numpy()
     eemb, _ = oenc.forward(flat.astype(np.float64), series, bf16=True)
@@ -74,18 +78,19 @@ def test_save_load_roundtrip(kw, tmp_path):
 
 @pytest.mark.parametrize("kind", [0, 1])
 def test_training_and_learned_scan(kw, kind):
-    """Training lowers the loss; the learned scan equals the oracle; and the
-    trained encoder needs fewer exact programs than an untrained one."""
+    """Training lowers the loss; the learned scan equals the oracle; and with a
+    proposal budget of k series, the trained encoder's proposals give a
+    tighter threshold than an untrained encoder's: fewer exact programs."""
     w = make_workload(n_series=4000, n_queries=24, d=3, length=96, n_classes=10, seed=21)
     db = kw.KnnDB(cuda(w.db), w.db_off)
     band, k = 0.1, 5
     oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=float(np.float32(band)),
                              kind=kind, k=k)
 
-    def scan(enc):
+    def scan(enc, seeds):
         enc.attach(db)
         ids, dist, st = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind,
-                                seed=kw.SEED_LEARNED, seed_count=32, stats=True)
+                                seed=kw.SEED_LEARNED, seed_count=seeds, stats=True)
         ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
         for q in range(w.n_queries):
             assert list(ids[q]) == list(oids[q])
@@ -93,12 +98,16 @@ def test_training_and_learned_scan(kw, kind):
         return st
 
     untrained = kw.Encoder(3, seed=1)
-    st0 = scan(untrained)
+    st0 = scan(untrained, k)
     trained = kw.Encoder(3, seed=1)
     tr = trained.train(db, 20000, epochs=6, batch_pairs=512, lr=2e-3, distance=kind, band=band)
     assert tr["final_loss"] < 0.5 * tr["first_loss"], tr
-    st1 = scan(trained)
-    assert st1["seeds"] == st0["seeds"] == 24 * 32
-    # what the trained network gains: fewer exact programs after the seeds
+    st1 = scan(trained, k)
+    st2 = scan(trained, 64)
+    for name, st in (("untrained", st0), ("trained", st1), ("trained64", st2)):
+        print("GAIN", name, kind, {x: st[x] for x in ("seeds", "seed_cells", "lb_pruned",
+                                                     "dp_calls", "dp_abandoned", "dp_cells")})
+    assert st1["seeds"] == st0["seeds"] == 24 * k
+    # what the trained network gains: fewer exact programs after the proposals
     assert st1["dp_calls"] < st0["dp_calls"], (st0, st1)
     db.close()
