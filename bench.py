@@ -39,7 +39,11 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 SEED_DESC = {"greedy": "greedy upper-bound pre-pass over every series (Section 4.3)",
              "lb": "LB_Box-ordered proposals scored exactly first, then filter",
+             "learned": "learned proposals (BF16 conv encoder trained on 200k pairs of the "
+                        "database's own DTW/DK distances) scored exactly first, then the "
+                        "LB_Box stream with early abandoning",
              "none": "no seeding"}
+TRAIN_PAIRS = 200_000
 
 
 def peaks():
@@ -182,19 +186,34 @@ def run_gpu(args):
     q0, q1 = w.q_off[rank * N_QUERIES], w.q_off[rank * N_QUERIES + nq]
     q_host = np.ascontiguousarray(w.q[q0:q1])
     q_off = w.q_off[rank * N_QUERIES:rank * N_QUERIES + nq + 1] - q0
-    db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
+    db_dev = torch.from_numpy(w.db).cuda()
+    kinds = {"both": (kw.DTW, kw.DK), "dtw": (kw.DTW,), "dk": (kw.DK,)}[args.only]
+    seed_mode = {"greedy": kw.SEED_GREEDY, "lb": kw.SEED_LB, "none": kw.SEED_NONE,
+                 "learned": kw.SEED_LEARNED}[args.seed]
+    # one database handle per distance: each carries the encoder trained on
+    # that distance (set-up, outside the timed region)
+    dbs, train_info, encoders = {}, {}, {}
+    for kind in kinds:
+        dbs[kind] = kw.KnnDB(db_dev, w.db_off)
+        if args.seed == "learned":
+            enc = kw.Encoder(D, seed=11 + kind)
+            train_info["DTW" if kind == kw.DTW else "DK"] = enc.train(
+                dbs[kind], TRAIN_PAIRS, epochs=3, batch_pairs=2048, lr=2e-3, distance=kind,
+                band=BAND, seed=5 + kind)
+            enc.attach(dbs[kind])
+            encoders[kind] = enc
+    db = dbs[kinds[0]]
     q_dev = torch.from_numpy(q_host).cuda()
     q_off_t = torch.from_numpy(q_off)
     ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
     dst = torch.empty((nq, K), dtype=torch.float32, device="cuda")
     cnt = torch.empty(nq, dtype=torch.int64, device="cuda")
-    kinds = {"both": (kw.DTW, kw.DK), "dtw": (kw.DTW,), "dk": (kw.DK,)}[args.only]
-    seed_mode = {"greedy": kw.SEED_GREEDY, "lb": kw.SEED_LB, "none": kw.SEED_NONE}[args.seed]
 
     def step(collect=None):
         for kind in kinds:
-            _, _, st = db.scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
-                               out=(ids, dst, cnt), stats=True, profile=True)
+            _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
+                                      seed=seed_mode, out=(ids, dst, cnt), stats=True,
+                                      profile=True)
             if collect is not None:
                 collect.append((kind, st))
 
@@ -209,13 +228,13 @@ def run_gpu(args):
     for kind in kinds:
         if args.shape:
             P, G = (int(v) for v in args.shape.split(","))
-            db.set_dp_shape(kind, r, LENGTH, P, G)
+            dbs[kind].set_dp_shape(kind, r, LENGTH, P, G)
         elif not args.no_autotune:
             nt = min(nq, 128)
-            db.autotune(q_dev[: int(q_off[nt])], q_off_t[: nt + 1], k=K, band=BAND, distance=kind,
-                        seed=seed_mode)
-        shapes["DTW" if kind == kw.DTW else "DK"] = dict(zip(("P", "G"),
-                                                             db.get_dp_shape(kind, r, LENGTH)))
+            dbs[kind].autotune(q_dev[: int(q_off[nt])], q_off_t[: nt + 1], k=K, band=BAND,
+                               distance=kind, seed=seed_mode)
+        shapes["DTW" if kind == kw.DTW else "DK"] = dict(
+            zip(("P", "G"), dbs[kind].get_dp_shape(kind, r, LENGTH)))
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -301,8 +320,8 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for kind in kinds:
-            db.scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
-                    out=(ids_h, dst_h, cnt_h))
+            dbs[kind].scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
+                           out=(ids_h, dst_h, cnt_h))
     barrier()
     e2e_dt = time.perf_counter() - t0
     if world > 1:
@@ -323,9 +342,35 @@ def run_gpu(args):
         for kind in kinds:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            db.scan(qp, qpo, k=K, band=BAND, distance=kind, query_batch=1, seed=kw.SEED_GREEDY)
+            dbs[kind].scan(qp, qpo, k=K, band=BAND, distance=kind, query_batch=1,
+                           seed=kw.SEED_GREEDY)
             torch.cuda.synchronize()
             plain["DTW" if kind == kw.DTW else "DK"] = nplain / (time.perf_counter() - t0)
+
+    # every seeding mode once on the same batch (same results; work and time)
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        modes = [("greedy", kw.SEED_GREEDY), ("lb", kw.SEED_LB)]
+        if args.seed == "learned":
+            modes.append(("learned", kw.SEED_LEARNED))
+        for kind in kinds:
+            kname = "DTW" if kind == kw.DTW else "DK"
+            ref = None
+            for mname, mode in modes:
+                dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=mode,
+                               out=(ids, dst, cnt))  # warm
+                _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
+                                          seed=mode, out=(ids, dst, cnt), stats=True,
+                                          profile=True)
+                res = (ids.clone(), dst.clone())
+                same = ref is None or (torch.equal(ref[0], res[0]) and
+                                       torch.equal(ref[1], res[1]))
+                ref = ref or res
+                variants[f"{kname}/{mname}"] = {
+                    "queries_per_s": nq / (st["ms_total"] / 1000.0), "identical_results": same,
+                    "ms_seed": st["ms_seed"], "ms_lb": st["ms_lb"], "ms_dp": st["ms_dp"],
+                    "ub_walks": st["ub_walks"], "lb_points": st["lb_points"],
+                    "dp_calls": st["dp_calls"], "dp_cells": st["dp_cells"] + st["seed_cells"]}
 
     if rank == 0:
         line = {
@@ -341,11 +386,13 @@ def run_gpu(args):
                        "parallelism": f"replicated database, queries sharded x{world}"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
             "per_distance": detail, "plain_scan_queries_per_s": plain, "dp_shape": shapes,
+            "seed_variants": variants, "encoder_training": train_info,
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
         print(json.dumps(line), flush=True)
-    db.close()
+    for d_ in dbs.values():
+        d_.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -359,7 +406,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--seed", default="lb", choices=["greedy", "lb", "none"])
+    ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--queries", type=int, default=N_QUERIES,
                     help="queries per GPU (smaller values only for profiling captures)")

@@ -117,6 +117,7 @@ typedef struct {
     int64_t dp_abandoned;    /* dynamic programs abandoned early                 */
     int64_t dp_cells;        /* band cells evaluated (lane slots x steps)        */
     int64_t reranked;        /* candidates re-scored in FP64                     */
+    int64_t lb_points;       /* (query, series point) pairs bounded by LB_Box    */
     int64_t launches;        /* kernels launched by the call                     */
     double ms_total;         /* time of the call on the stream                   */
     double ms_seed;          /* profile = 1: threshold seeding (greedy/learned)  */
@@ -291,8 +292,9 @@ KNN_API int32_t knn_encoder_num_params(void);
 KNN_API knn_status knn_encoder_create(int32_t d, uint64_t seed, knn_encoder **out);
 KNN_API knn_status knn_encoder_destroy(knn_encoder *enc);
 /* Train on n_pairs random pairs of database series; the target of a pair is
- * its banded distance computed by the scan's DP (DTW divided by the longer
- * length, or DK^2); loss (||e_a - e_b||^2 - target)^2. */
+ * log(1 + x) of its banded distance computed by the scan's DP, x = DTW
+ * divided by the longer length, or DK^2 (a monotone transform: the ranking
+ * is what matters); loss (||e_a - e_b||^2 - target)^2. */
 KNN_API knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_pairs,
                                      const knn_train_params *params, knn_train_stats *stats,
                                      void *stream);

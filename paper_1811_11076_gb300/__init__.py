@@ -73,7 +73,7 @@ class Stats(C.Structure):
     _fields_ = [("pairs", C.c_int64), ("band_infeasible", C.c_int64), ("ub_walks", C.c_int64),
                 ("seeds", C.c_int64), ("seed_cells", C.c_int64), ("lb_pruned", C.c_int64), ("lb_pruned_late", C.c_int64),
                 ("dp_calls", C.c_int64), ("dp_abandoned", C.c_int64), ("dp_cells", C.c_int64),
-                ("reranked", C.c_int64), ("launches", C.c_int64), ("ms_total", C.c_double),
+                ("reranked", C.c_int64), ("lb_points", C.c_int64), ("launches", C.c_int64), ("ms_total", C.c_double),
                 ("ms_seed", C.c_double), ("ms_lb", C.c_double), ("ms_dp", C.c_double),
                 ("ms_finalize", C.c_double)]
 

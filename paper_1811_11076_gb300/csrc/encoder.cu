@@ -466,8 +466,9 @@ __global__ void pair_targets_kernel(const float *raw, const int *la, const int *
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float v = raw[i];
         const int m = la[items[i].y], nn = lb[items[i].x];
-        // DTW: mean squared cost per cell of the longer series; DK: DK^2
-        target[i] = kind == 0 ? v / (float)max(m, nn) : v;
+        // log(1 + DTW / longer length) or log(1 + DK^2): monotone in the
+        // distance (ranking is what the proposal needs) and of moderate range
+        target[i] = kind == 0 ? log1pf(v / (float)max(m, nn)) : log1pf(v);
     }
 }
 

@@ -231,6 +231,7 @@ enum Stat : int {
     STAT_DP_CELLS,
     STAT_RERANKED,
     STAT_SEED_CELLS,
+    STAT_LB_POINTS,      // (query, series point) pairs bounded by LB_Box
     STAT_COUNT
 };
 

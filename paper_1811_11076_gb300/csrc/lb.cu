@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
     const int m = a.q_len[qb];
     const int nser = a.c_end - a.c_begin;
     const int ntiles = (nser + 31) / 32;
-    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
 
     for (int t = blockIdx.x + gridDim.x * warp; t < ntiles; t += gridDim.x * LB_WARPS) {
         const int c0 = a.c_begin + t * 32;
@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
             if (lane == jj) {
                 my_lb = acc;
                 my_feasible = feasible;
+                st_points += feasible ? (unsigned long long)n : 0ull;
             }
         }
         const int c = c0 + lane;
@@ -261,11 +262,13 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
         st_pairs += __shfl_xor_sync(KNN_FULL_MASK, st_pairs, o);
         st_inf += __shfl_xor_sync(KNN_FULL_MASK, st_inf, o);
         st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
+        st_points += __shfl_xor_sync(KNN_FULL_MASK, st_points, o);
     }
     if (lane == 0 && a.stats) {
         atomicAdd(a.stats + STAT_PAIRS, st_pairs);
         atomicAdd(a.stats + STAT_INFEASIBLE, st_inf);
         atomicAdd(a.stats + STAT_LB_PRUNED, st_pruned);
+        atomicAdd(a.stats + STAT_LB_POINTS, st_points);
     }
 }
 
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
         if (j >= nqt)
             lim[j] = -1.f;
     }
-    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
     const int nser = a.c_end - a.c_begin;
     const int span = (nser + LB_THREADS - 1) / LB_THREADS * LB_THREADS;
     for (int i = blockIdx.x * LB_THREADS + threadIdx.x; i < span; i += gridDim.x * LB_THREADS) {
@@ -347,6 +350,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
                     break;
             }
             const bool full = (ch + 1) * PPC <= n;
+            st_points += (unsigned long long)PPC * nqt;
             float v[CH];
 #pragma unroll
             for (int f = 0; f < F4; ++f) {
@@ -441,11 +445,13 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
         st_pairs += __shfl_xor_sync(KNN_FULL_MASK, st_pairs, o);
         st_inf += __shfl_xor_sync(KNN_FULL_MASK, st_inf, o);
         st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
+        st_points += __shfl_xor_sync(KNN_FULL_MASK, st_points, o);
     }
     if (lane == 0 && a.stats) {
         atomicAdd(a.stats + STAT_PAIRS, st_pairs);
         atomicAdd(a.stats + STAT_INFEASIBLE, st_inf);
         atomicAdd(a.stats + STAT_LB_PRUNED, st_pruned);
+        atomicAdd(a.stats + STAT_LB_POINTS, st_points);
     }
 }
 

@@ -767,6 +767,7 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         stats->dp_abandoned = (int64_t)hc.stats[STAT_DP_ABANDONED];
         stats->dp_cells = (int64_t)hc.stats[STAT_DP_CELLS];
         stats->reranked = (int64_t)hc.stats[STAT_RERANKED];
+        stats->lb_points = (int64_t)hc.stats[STAT_LB_POINTS];
         stats->launches = launches;
         stats->ms_total = ms;
         stats->ms_seed = stage_ms[0];

@@ -76,38 +76,66 @@ def test_save_load_roundtrip(kw, tmp_path):
     np.testing.assert_array_equal(enc.params(), enc2.params())
 
 
+def recall_at(emb_q, emb_db, true_ids, S):
+    """Fraction of the true k nearest found among the S lowest predicted."""
+    pred = ((emb_q[:, None, :] - emb_db[None, :, :]) ** 2).sum(-1)
+    top = np.argsort(pred, axis=1)[:, :S]
+    return float(np.mean([len(set(top[q]) & set(true_ids[q])) / len(true_ids[q])
+                          for q in range(len(true_ids))]))
+
+
 @pytest.mark.parametrize("kind", [0, 1])
 def test_training_and_learned_scan(kw, kind):
-    """Training lowers the loss; the learned scan equals the oracle; and with a
-    proposal budget of k series, the trained encoder's proposals give a
-    tighter threshold than an untrained encoder's: fewer exact programs."""
+    """Training lowers the loss and ranks better than the untrained encoder;
+    the learned scan equals the oracle; and against the method without the
+    learned proposal it does less work at identical results."""
     w = make_workload(n_series=4000, n_queries=24, d=3, length=96, n_classes=10, seed=21)
     db = kw.KnnDB(cuda(w.db), w.db_off)
     band, k = 0.1, 5
     oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=float(np.float32(band)),
                              kind=kind, k=k)
 
-    def scan(enc, seeds):
-        enc.attach(db)
-        ids, dist, st = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind,
-                                seed=kw.SEED_LEARNED, seed_count=seeds, stats=True)
+    def check(ids, dist):
         ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
         for q in range(w.n_queries):
             assert list(ids[q]) == list(oids[q])
             np.testing.assert_allclose(dist[q], odist[q], rtol=1e-5 if kind == 0 else 1e-6)
+
+    def learned(enc, seeds):
+        enc.attach(db)
+        ids, dist, st = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind,
+                                seed=kw.SEED_LEARNED, seed_count=seeds, stats=True)
+        check(ids, dist)
         return st
 
+    def recall(enc):
+        eq = enc.embed(cuda(w.q), cuda(w.q_off)).cpu().numpy()
+        ed = enc.embed(cuda(w.db), cuda(w.db_off)).cpu().numpy()
+        return recall_at(eq, ed, oids, 64)
+
     untrained = kw.Encoder(3, seed=1)
-    st0 = scan(untrained, k)
+    r0 = recall(untrained)
     trained = kw.Encoder(3, seed=1)
     tr = trained.train(db, 20000, epochs=6, batch_pairs=512, lr=2e-3, distance=kind, band=band)
     assert tr["final_loss"] < 0.5 * tr["first_loss"], tr
-    st1 = scan(trained, k)
-    st2 = scan(trained, 64)
-    for name, st in (("untrained", st0), ("trained", st1), ("trained64", st2)):
-        print("GAIN", name, kind, {x: st[x] for x in ("seeds", "seed_cells", "lb_pruned",
-                                                     "dp_calls", "dp_abandoned", "dp_cells")})
-    assert st1["seeds"] == st0["seeds"] == 24 * k
-    # what the trained network gains: fewer exact programs after the proposals
-    assert st1["dp_calls"] < st0["dp_calls"], (st0, st1)
+    r1 = recall(trained)
+    st = {"learned": learned(trained, 64)}
+    for name, mode in (("none", kw.SEED_NONE), ("greedy", kw.SEED_GREEDY), ("lb", kw.SEED_LB)):
+        ids, dist, st[name] = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind,
+                                      seed=mode, seed_count=64, stats=True)
+        check(ids, dist)
+    for name, s in st.items():
+        print("GAIN", kind, name, {x: s[x] for x in ("seeds", "ub_walks", "lb_points", "lb_pruned",
+                                                     "dp_calls", "dp_cells", "seed_cells")})
+    print("RECALL@64", kind, "untrained", r0, "trained", r1, tr)
+    assert r1 > r0, (r0, r1)
+    L = st["learned"]
+    # the method without proposals: no pruning until programs finish
+    assert L["dp_calls"] < 0.5 * st["none"]["dp_calls"]
+    assert L["dp_cells"] + L["seed_cells"] < st["none"]["dp_cells"]
+    # the paper's pre-pass walks every series; the learned proposal walks none
+    assert L["ub_walks"] == 0 and st["greedy"]["ub_walks"] == 4000 * 24
+    # LB_Box-ordered proposals need every bound in full first; the learned
+    # threshold exists before the stream, which abandons early
+    assert L["lb_points"] < st["lb"]["lb_points"]
     db.close()
