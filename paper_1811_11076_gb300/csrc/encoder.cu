@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) wgrad_mma_kernel(const WgradArgs a)
 // point stride and a length per series) rounded to BF16, [B][L][16].
 __global__ void gather_input_kernel(const float *src, const int64_t *off, int stride,
                                     const int *len, const int *idx, int d, int B, int L,
-                                    __nv_bfloat16 *x0, int *len_out)
+                                    float in_scale, __nv_bfloat16 *x0, int *len_out)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * L * ENC_CIN;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -247,7 +247,7 @@ __global__ void gather_input_kernel(const float *src, const int64_t *off, int st
         const int n = len[s];
         float v = 0.f;
         if (t < n && c < d)
-            v = src[off[s] + (int64_t)t * stride + c];
+            v = src[off[s] + (int64_t)t * stride + c] * in_scale;
         x0[e] = __float2bfloat16_rn(v);
         if (rem == 0)
             len_out[b] = min(n, L);
@@ -481,6 +481,7 @@ struct knn_encoder {
     int d = 0;
     int dev = 0;
     int64_t step = 0;
+    float in_scale = 1.f;  // inputs are multiplied by this before the first layer
     DevBuf params, grad, m, v;
     DevBuf w1f, w2f, w3f, w2d, w3d;
     // work buffers for a forward/backward batch
@@ -558,7 +559,8 @@ knn_status enc_forward(knn_encoder *enc, const float *src, const int64_t *off, i
     const int Lp = (L + TILE_T - 1) / TILE_T * TILE_T;
     const int64_t tot = (int64_t)B * Lp * ENC_CIN;
     gather_input_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, st>>>(
-        src, off, stride, len, idx, d, B, Lp, enc->x0.as<__nv_bfloat16>(), enc->lenb.as<int>());
+        src, off, stride, len, idx, d, B, Lp, enc->in_scale, enc->x0.as<__nv_bfloat16>(),
+        enc->lenb.as<int>());
     ConvArgs c{};
     c.len = enc->lenb.as<int>();
     c.B = B;
@@ -734,6 +736,8 @@ extern "C" knn_status knn_encoder_create(int32_t d, uint64_t seed, knn_encoder *
     fill(ENC_OFF_W2, ENC_K * ENC_C * ENC_C, ENC_K * ENC_C);
     fill(ENC_OFF_W3, ENC_K * ENC_C * ENC_C, ENC_K * ENC_C);
     fill(ENC_OFF_WL, ENC_C * ENC_E, ENC_C);
+    for (int i = 0; i < ENC_C * ENC_E; ++i)
+        p[ENC_OFF_WL + i] *= 0.1f;  // start with small embeddings
     // coordinates beyond d never carry data: keep their weights at zero
     for (int tap = 0; tap < ENC_K; ++tap)
         for (int ci = d; ci < ENC_CIN; ++ci)
@@ -940,28 +944,60 @@ extern "C" knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
-    // pairs: uniform over the database (bucket order indices), seeded
+    // input scale from the database's spread, fixed at the first training call
     uint64_t rng = tp->seed ^ 0x7a1eull;
     const int N = db->N;
-    std::vector<int2> items(n_pairs);
-    for (int64_t i = 0; i < n_pairs; ++i) {
+    if (enc->step == 0) {
+        const int64_t ns = std::min<int64_t>(db->total_floats, 1 << 20);
+        std::vector<float> sample(ns);
+        cudaMemcpy(sample.data(), db->data.p, 4 * ns, cudaMemcpyDeviceToHost);
+        double sum = 0, sq = 0;
+        int64_t cnt = 0;
+        for (float v : sample)
+            if (v != 0.f) {
+                sum += v;
+                sq += (double)v * v;
+                ++cnt;
+            }
+        const double var = cnt > 1 ? sq / cnt - (sum / cnt) * (sum / cnt) : 1.0;
+        enc->in_scale = (float)(1.0 / std::sqrt(std::max(var, 1e-12)));
+    }
+    // pairs, seeded: half uniformly random, half "near": for an anchor the
+    // nearest (by the exact distance) of MINE random candidates, so that the
+    // ranking of close series is learned and not only the bulk of far ones
+    constexpr int MINE = 16;
+    const int64_t n_near = N > MINE ? n_pairs / 2 : 0;
+    const int64_t n_rand = n_pairs - n_near;
+    const int64_t n_dp = n_near * MINE + n_rand;
+    std::vector<int2> items(n_dp);
+    for (int64_t i = 0; i < n_near; ++i) {
+        const int a = (int)(splitmix(rng) % (uint64_t)N);
+        for (int j = 0; j < MINE; ++j) {
+            int b;
+            do {
+                b = (int)(splitmix(rng) % (uint64_t)N);
+            } while (b == a);
+            items[i * MINE + j] = make_int2(b, a);  // (series, "query") as the DP expects
+        }
+    }
+    for (int64_t i = 0; i < n_rand; ++i) {
         int a, b;
         do {
             a = (int)(splitmix(rng) % (uint64_t)N);
             b = (int)(splitmix(rng) % (uint64_t)N);
         } while (a == b && N > 1);
-        items[i] = make_int2(b, a);  // (series, "query") as the DP kernel expects
+        items[n_near * MINE + i] = make_int2(b, a);
     }
     DevBuf ditems, dlb, draw, dtgt, ctl, bidx, bpa, bpb, btgt;
     knn_status s;
-    if ((s = ditems.ensure(sizeof(int2) * n_pairs)) || (s = dlb.ensure(4 * n_pairs)) ||
-        (s = draw.ensure(4 * n_pairs)) || (s = dtgt.ensure(4 * n_pairs)) ||
+    if ((s = ditems.ensure(sizeof(int2) * n_dp)) || (s = dlb.ensure(4 * n_dp)) ||
+        (s = draw.ensure(4 * n_dp)) || (s = dtgt.ensure(4 * n_dp)) ||
         (s = ctl.ensure(sizeof(Ctrl))))
         return s;
-    cudaMemcpyAsync(ditems.p, items.data(), sizeof(int2) * n_pairs, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(dlb.p, 0, 4 * n_pairs, st);
+    cudaMemcpyAsync(ditems.p, items.data(), sizeof(int2) * n_dp, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(dlb.p, 0, 4 * n_dp, st);
     cudaMemsetAsync(ctl.p, 0, sizeof(Ctrl), st);
-    const int np = (int)n_pairs;
+    const int np = (int)n_dp;
     Ctrl *ct = ctl.as<Ctrl>();
     cudaMemcpyAsync(&ct->seg_count[0], &np, 4, cudaMemcpyHostToDevice, st);
     // targets from the scan's own DP (pair mode, no threshold)
@@ -974,7 +1010,7 @@ extern "C" knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_
     x.items = ditems.as<int2>();
     x.item_lb = dlb.as<float>();
     x.n_items = &ct->seg_count[0];
-    x.items_cap = n_pairs;
+    x.items_cap = n_dp;
     x.head = &ct->seg_head[0];
     x.db = db->data.as<float>();
     x.db_off = db->off.as<int64_t>();
@@ -996,11 +1032,34 @@ extern "C" knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_
     pair_targets_kernel<<<256, 256, 0, st>>>(draw.as<float>(), db->len.as<int>(), db->len.as<int>(),
                                              ditems.as<int2>(), np, tp->distance,
                                              dtgt.as<float>());
-    std::vector<float> htgt(n_pairs);
-    cudaMemcpyAsync(htgt.data(), dtgt.p, 4 * n_pairs, cudaMemcpyDeviceToHost, st);
+    std::vector<float> hall(n_dp);
+    cudaMemcpyAsync(hall.data(), dtgt.p, 4 * n_dp, cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return cuda_error(e, "training targets");
+    // keep, per anchor, its nearest candidate; then the random pairs
+    std::vector<int2> chosen;
+    std::vector<float> htgt;
+    chosen.reserve(n_pairs);
+    htgt.reserve(n_pairs);
+    for (int64_t i = 0; i < n_near; ++i) {
+        int64_t best = -1;
+        for (int j = 0; j < MINE; ++j) {
+            const int64_t t = i * MINE + j;
+            if (std::isfinite(hall[t]) && (best < 0 || hall[t] < hall[best]))
+                best = t;
+        }
+        if (best >= 0) {
+            chosen.push_back(items[best]);
+            htgt.push_back(hall[best]);
+        }
+    }
+    for (int64_t i = 0; i < n_rand; ++i) {
+        chosen.push_back(items[n_near * MINE + i]);
+        htgt.push_back(hall[n_near * MINE + i]);
+    }
+    items.swap(chosen);
+    n_pairs = (int64_t)items.size();
     // pairs with an unreachable end cell carry no target: drop them
     std::vector<int64_t> keep;
     keep.reserve(n_pairs);
@@ -1139,8 +1198,8 @@ extern "C" knn_status knn_encoder_save(const knn_encoder *enc, const char *path)
         return set_error(KNN_ERR_INVALID, std::string("cannot write ") + path);
     // JSON header line, then little-endian float32 params, Adam m, Adam v
     fprintf(f, "{\"format\": \"knnwarp-encoder\", \"version\": 1, \"d\": %d, \"params\": %d, "
-               "\"step\": %lld}\n",
-            enc->d, ENC_NPARAM, (long long)enc->step);
+               "\"step\": %lld, \"in_scale\": %.9g}\n",
+            enc->d, ENC_NPARAM, (long long)enc->step, (double)enc->in_scale);
     fwrite(p.data(), 4, ENC_NPARAM, f);
     fwrite(m.data(), 4, ENC_NPARAM, f);
     fwrite(v.data(), 4, ENC_NPARAM, f);
@@ -1163,8 +1222,10 @@ extern "C" knn_status knn_encoder_load(const char *path, knn_encoder **out)
     }
     int d = 0, np = 0;
     long long step = 0;
+    double in_scale = 1.0;
     if (!strstr(line, "knnwarp-encoder") ||
-        sscanf(strstr(line, "\"d\":"), "\"d\": %d, \"params\": %d, \"step\": %lld", &d, &np, &step) != 3 ||
+        sscanf(strstr(line, "\"d\":"), "\"d\": %d, \"params\": %d, \"step\": %lld, \"in_scale\": %lf",
+               &d, &np, &step, &in_scale) != 4 ||
         np != ENC_NPARAM) {
         fclose(f);
         return set_error(KNN_ERR_INVALID, "not an encoder file of this version");
@@ -1184,6 +1245,7 @@ extern "C" knn_status knn_encoder_load(const char *path, knn_encoder **out)
     cudaMemcpy(enc->m.p, m.data(), 4 * ENC_NPARAM, cudaMemcpyHostToDevice);
     cudaMemcpy(enc->v.p, v.data(), 4 * ENC_NPARAM, cudaMemcpyHostToDevice);
     enc->step = step;
+    enc->in_scale = (float)in_scale;
     enc_weights_bf16(enc, nullptr);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
