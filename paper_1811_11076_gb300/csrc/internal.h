@@ -104,6 +104,8 @@ struct SelArgs {
     float *seed_lb;
     int *n_seed;
     int seed_cap;
+    uint32_t *seed_bits;       // nullable: [nq][bits_words] bit per chosen series
+    int bits_words;
     unsigned long long *stats;
     int *status;
 };

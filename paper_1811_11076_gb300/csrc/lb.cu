@@ -419,7 +419,10 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
             st_pairs += valid;
             st_inf += valid && !feasible;
             if (a.items) {
-                const bool keep = feasible && lb <= lim[j];
+                bool seeded = false;
+                if (a.skip && valid)
+                    seeded = (a.skip[(int64_t)qb * a.skip_words + (c >> 5)] >> (c & 31)) & 1u;
+                const bool keep = feasible && !seeded && lb <= lim[j];
                 st_pruned += feasible && !keep;
                 const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
                 if (kb) {

@@ -192,6 +192,7 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(out_counts, sizeof(int64_t) * nq);
     if (pl.seeded && p_learned(pl)) {
         G_(scores, sizeof(float) * nq * (size_t)db->N);
+        G_(skip, sizeof(uint32_t) * nq * (size_t)((db->N + 31) / 32));
         G_(qemb, sizeof(uint16_t) * nq * 64);
         G_(qnorm, sizeof(float) * nq);
         if ((s = enc_work(db->enc, nq, pl.max_m)))
@@ -323,8 +324,11 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         sa.seed_lb = ws.seed_lb.as<float>();
         sa.n_seed = &ctrl->n_seed;
         sa.seed_cap = nq * pl.S;
+        sa.seed_bits = ws.skip.as<uint32_t>();
+        sa.bits_words = (db->N + 31) / 32;
         sa.stats = stats;
         sa.status = &ctrl->status;
+        cudaMemsetAsync(ws.skip.p, 0, sizeof(uint32_t) * nq * (size_t)sa.bits_words, st);
         launch_select(sa, st);
         DpArgs a = dp_args(db, pl, p, ws.seed_items.as<int2>(), ws.seed_lb.as<float>(),
                            &ctrl->n_seed, (int64_t)nq * pl.S, &ctrl->seed_head);
@@ -376,6 +380,10 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
             l.out_lb = ws.lb_all.as<float>();
             l.out_lb_stride = db->N;
         } else {
+            if (pl.learned) {
+                l.skip = ws.skip.as<uint32_t>();
+                l.skip_words = (db->N + 31) / 32;
+            }
             l.items = ws.items.as<int2>() + sg.base;
             l.item_lb = ws.item_lb.as<float>() + sg.base;
             l.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];

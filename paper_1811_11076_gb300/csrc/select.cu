@@ -74,6 +74,9 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
                 a.seed_lb[pos] = lb ? lb[c] : 0.f;
                 if (lb)
                     lb[c] = -1.f;  // scored as a seed; the filter skips it
+                if (a.seed_bits)   // scored as a seed; the LB_Box stream skips it
+                    atomicOr(a.seed_bits + (int64_t)q * a.bits_words + ((a.c_base + c) >> 5),
+                             1u << ((a.c_base + c) & 31));
                 atomicAdd(&s_count, 1);
             } else {
                 atomicOr(a.status, KNN_DEV_CAPACITY);
