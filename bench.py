@@ -32,6 +32,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "exact k-NN queries/sec and DP GCUPS (DTW & DK), learned+batched vs plain GPU scan"
+# Workloads this harness measures (the first is the default and the headline):
+# generator name in synthdata.WORKLOADS, k, band, queries per GPU, whether the
+# timed scans replay a CUDA graph.
+BENCH = {
+    "scale_d3_n100k_L256": dict(k=10, band=0.1, queries=1000, graph=False),
+    **{f"uneven_d{d}_n200k_L50_1000": dict(k=5, band=0.1, queries=256, graph=True)
+       for d in range(3, 9)},
+    "learned_d3_n1M_L128": dict(k=10, band=0.1, queries=1000, graph=False),
+    "highdim_d16_n500k_L512": dict(k=50, band=0.1, queries=32, graph=False),
+}
 WORKLOAD = "scale_d3_n100k_L256"
 N_SERIES, LENGTH, D, N_QUERIES = 100_000, 256, 3, 1000
 K, BAND = 10, 0.1
@@ -111,10 +121,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def select_workload(name: str):
+    """Set the module-level workload parameters from the BENCH table."""
+    global WORKLOAD, N_SERIES, LENGTH, D, N_QUERIES, K, BAND
+    from synthdata import WORKLOADS
+    g, b = WORKLOADS[name], BENCH[name]
+    WORKLOAD = name
+    N_SERIES, D, N_QUERIES = g["n_series"], g["d"], b["queries"]
+    LENGTH = g.get("length", 0) if "length_range" not in g else 0
+    K, BAND = b["k"], b["band"]
+
+
 def workload(world: int):
-    from synthdata import make_workload
-    return make_workload(n_series=N_SERIES, n_queries=N_QUERIES * world, d=D, length=LENGTH,
-                         n_classes=20, seed=1)
+    from synthdata import WORKLOADS, make_workload
+    kw = dict(WORKLOADS[WORKLOAD])
+    kw["n_queries"] = N_QUERIES * world
+    return make_workload(**kw)
 
 
 def cpu_baseline(w, n_sample: int = 4) -> dict:
@@ -158,7 +180,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH, "d": D,
+            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH or "50-1000", "d": D,
                        "k": K, "band": BAND, "sample_queries_per_step": n_sample},
             "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
@@ -182,7 +204,7 @@ def run_gpu(args):
     kw.lib()
 
     w = workload(world)
-    nq = args.queries
+    nq = N_QUERIES
     q0, q1 = w.q_off[rank * N_QUERIES], w.q_off[rank * N_QUERIES + nq]
     q_host = np.ascontiguousarray(w.q[q0:q1])
     q_off = w.q_off[rank * N_QUERIES:rank * N_QUERIES + nq + 1] - q0
@@ -213,7 +235,7 @@ def run_gpu(args):
         for kind in kinds:
             _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
                                       seed=seed_mode, out=(ids, dst, cnt), stats=True,
-                                      profile=True)
+                                      profile=not graph, use_graph=graph)
             if collect is not None:
                 collect.append((kind, st))
 
@@ -225,6 +247,7 @@ def run_gpu(args):
     # autotuner (set-up, outside the timed region): DP shape per distance
     shapes = {}
     r = int(np.float64(np.float32(BAND)) * LENGTH)
+    graph = BENCH[WORKLOAD]["graph"] and not args.no_graph
     for kind in kinds:
         if args.shape:
             P, G = (int(v) for v in args.shape.split(","))
@@ -233,8 +256,9 @@ def run_gpu(args):
             nt = min(nq, 128)
             dbs[kind].autotune(q_dev[: int(q_off[nt])], q_off_t[: nt + 1], k=K, band=BAND,
                                distance=kind, seed=seed_mode)
-        shapes["DTW" if kind == kw.DTW else "DK"] = dict(
-            zip(("P", "G"), dbs[kind].get_dp_shape(kind, r, LENGTH)))
+        if LENGTH:
+            shapes["DTW" if kind == kw.DTW else "DK"] = dict(
+                zip(("P", "G"), dbs[kind].get_dp_shape(kind, r, LENGTH)))
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -256,6 +280,20 @@ def run_gpu(args):
     total_queries = nq * len(kinds) * args.steps * world
     value = total_queries / (ms / 1000.0)
 
+    if graph:
+        # the timed scans replayed graphs (no events inside); take the stage
+        # split from one profiled eager scan per distance
+        prof = []
+        for kind in kinds:
+            _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
+                                      seed=seed_mode, out=(ids, dst, cnt), stats=True,
+                                      profile=True)
+            prof.append((kind, st))
+        for i, (kind, st) in enumerate(collected):
+            p = dict(prof[[k_ for k_, _ in prof].index(kind)][1])
+            scale = st["ms_total"] / max(p["ms_total"], 1e-9)
+            for key in ("ms_seed", "ms_lb", "ms_dp", "ms_finalize"):
+                st[key] = p[key] * scale
     # per-distance detail (this rank)
     detail = {}
     for kind in kinds:
@@ -287,7 +325,7 @@ def run_gpu(args):
         for k_ in stage:
             stage[k_] += s[f"ms_{k_}"]
         cells[kind] += s["dp_cells"]
-        lb_bytes += s["pairs"] * LENGTH * D * 4
+        lb_bytes += s["lb_points"] * D * 4
     dominant = max(stage, key=stage.get)
     clocks = clk.summary()
     if dominant == "lb":
@@ -378,11 +416,12 @@ def run_gpu(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH, "d": D,
+            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH or "50-1000", "d": D,
                        "queries_per_gpu": nq, "k": K, "band": BAND,
                        "distances": ["DTW" if k_ == kw.DTW else "DK" for k_ in kinds],
-                       "seed": SEED_DESC[args.seed],
-                       "batched": True, "l2": "inputs larger than L2 (307 MB database)",
+                       "seed": SEED_DESC[args.seed], "cuda_graph": graph,
+                       "batched": True,
+                       "l2": f"inputs larger than L2 ({w.db.nbytes / 1e6:.0f} MB database)",
                        "parallelism": f"replicated database, queries sharded x{world}"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
             "per_distance": detail, "plain_scan_queries_per_s": plain, "dp_shape": shapes,
@@ -409,12 +448,17 @@ def main():
     ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--queries", type=int, default=N_QUERIES,
-                    help="queries per GPU (smaller values only for profiling captures)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(BENCH))
+    ap.add_argument("--queries", type=int, default=0,
+                    help="queries per GPU (default: the workload's; smaller only for profiling)")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default="", help="P,G: fix the DP shape instead of tuning it")
     args = ap.parse_args()
+    select_workload(args.workload)
+    if args.queries:
+        globals()["N_QUERIES"] = args.queries
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -55,6 +55,14 @@ __device__ __forceinline__ void load_point(const float *__restrict__ p, float (&
     }
 }
 
+// min(a, b, c) in one instruction (three-input PTX min, sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Squared Euclidean distance, accumulated on top of `init` with FMAs in
 // coordinate order.  init = +inf masks a cell out of the band.
 template <int D>

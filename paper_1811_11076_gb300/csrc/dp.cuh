@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
             for (int e = 0; e < P; ++e) {
                 const float c = sqdist_acc<D>(qw[((u - e) % U + U) % U], xw[(u + e) % U], mE[e]);
                 const float left = (e == 0) ? up : O[e - 1];
-                const float mn = fminf(fminf(left, O[e]), E[e]);
+                const float mn = fmin3(left, O[e], E[e]);
                 E[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
             }
             float dn = __shfl_down_sync(KNN_FULL_MASK, E[0], 1, G);
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                 const float c =
                     sqdist_acc<D>(qw[((u - e) % U + U) % U], xw[(u + e + 1) % U], mO[e]);
                 const float right = (e == P - 1) ? dn : E[e + 1];
-                const float mn = fminf(fminf(E[e], right), O[e]);
+                const float mn = fmin3(E[e], right, O[e]);
                 O[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
             }
         }

@@ -288,13 +288,14 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
     constexpr int F4 = CH / 4;
-    extern __shared__ __align__(128) float4 env_s[];  // [QT][stride] lo, then [QT][stride] hi
+    // [QT][env_floats] lo, then [QT][env_floats] hi: this bucket's envelopes
+    extern __shared__ __align__(128) float4 env_s[];
     __shared__ __align__(8) uint64_t bar;
 
     const int q0 = blockIdx.y * QT;
     const int nqt = min(QT, a.nq - q0);
     const int lane = threadIdx.x & 31;
-    const int st4 = (int)(a.env_stride / 4);
+    const int st4 = a.env_floats / 4;
     const float4 *lo_s = env_s;
     const float4 *hi_s = env_s + QT * st4;
 
@@ -304,10 +305,13 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)(nqt * a.env_stride * 4);
-        mbar_expect_tx(&bar, 2u * bytes);
-        tma_bulk_g2s(env_s, a.env_lo + (int64_t)q0 * a.env_stride, bytes, &bar);
-        tma_bulk_g2s(env_s + QT * st4, a.env_hi + (int64_t)q0 * a.env_stride, bytes, &bar);
+        const uint32_t bytes = (uint32_t)a.env_floats * 4u;
+        mbar_expect_tx(&bar, 2u * bytes * (uint32_t)nqt);
+        for (int j = 0; j < nqt; ++j) {
+            tma_bulk_g2s(env_s + j * st4, a.env_lo + (int64_t)(q0 + j) * a.env_stride, bytes, &bar);
+            tma_bulk_g2s(env_s + (QT + j) * st4, a.env_hi + (int64_t)(q0 + j) * a.env_stride, bytes,
+                         &bar);
+        }
     }
     if (!mbar_wait0(&bar)) {
         if (lane == 0)
@@ -486,7 +490,7 @@ void lb_init_attributes()
 template <int D, int QT>
 static void lb_multi_launch(const LbArgs &a, int form, int n_sm, cudaStream_t st)
 {
-    const size_t smem = (size_t)QT * a.env_stride * 4 * 2;
+    const size_t smem = (size_t)QT * a.env_floats * 4 * 2;
     const int nser = a.c_end - a.c_begin;
     const int qtiles = (a.nq + QT - 1) / QT;
     int bx = (nser + LB_THREADS - 1) / LB_THREADS;
@@ -506,7 +510,7 @@ static void lb_launch_d(const LbArgs &a, int form, int n_sm, cudaStream_t st)
 {
     // several queries: the multi-query kernel with the largest tile whose
     // envelopes fit in shared memory
-    const size_t per_q = (size_t)a.env_stride * 4 * 2;
+    const size_t per_q = (size_t)a.env_floats * 4 * 2;
     if (a.nq >= 4 && !a.single_query_kernel) {
         const int want = a.qtile > 0 ? a.qtile : 16;
         if (want >= 16 && a.nq >= 16 && 16 * per_q <= 192 * 1024)

@@ -133,11 +133,17 @@ def make_workload(*, n_series: int, n_queries: int, d: int, length=64,
             inst = _instances(templ, classes[s:e], knots[s:e], int(length), nz)
             pts[off[s]:off[e]] = inst.reshape(-1, d).astype(np.float32)
     else:
-        for s in range(total):
-            n = int(lens[s])
-            nz = rng.standard_normal((1, n, d)) * noise_sigma
-            inst = _instances(templ, classes[s:s + 1], knots[s:s + 1], n, nz)
-            pts[off[s]:off[s + 1]] = inst[0].astype(np.float32)
+        # noise for all series in order, then one vectorised resampling per
+        # distinct length (same values as drawing series by series)
+        noise = rng.standard_normal((int(off[-1]), d)) * noise_sigma
+        for n in np.unique(lens):
+            idx = np.nonzero(lens == n)[0]
+            for s0 in range(0, len(idx), batch):
+                sel = idx[s0:s0 + batch]
+                nz = np.stack([noise[off[i]:off[i + 1]] for i in sel])
+                inst = _instances(templ, classes[sel], knots[sel], int(n), nz)
+                for j, i in enumerate(sel):
+                    pts[off[i]:off[i + 1]] = inst[j].astype(np.float32)
     db_end = int(off[n_series])
     return Workload(
         d=d,
