@@ -399,10 +399,12 @@ __global__ void emb_to_bf16_kernel(const float *e, const int *dst_index, int B,
 
 // Predicted distance ||e_q - e_c||^2 = |e_q|^2 + |e_c|^2 - 2 e_q.e_c for a
 // query tile (64) x series tile (64); the dot products on the tensor cores.
+// With tile_idx non-null only the lowest score of each 64-series tile and
+// its series are written per query ([nq][stride] with stride >= tiles).
 __global__ void __launch_bounds__(128) score_kernel(const __nv_bfloat16 *eq, const float *nq2,
                                                     int nq, const __nv_bfloat16 *ec,
                                                     const float *nc2, int n, float *score,
-                                                    int64_t stride)
+                                                    int *tile_idx, int64_t stride)
 {
     constexpr int S = ENC_E + 8;
     __shared__ __align__(16) __nv_bfloat16 Qs[64 * S];
@@ -446,17 +448,40 @@ __global__ void __launch_bounds__(128) score_kernel(const __nv_bfloat16 *eq, con
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int q = q0 + r0 + 8 * half;
-        if (q >= nq)
-            continue;
+        const float qn = q < nq ? nq2[q] : 0.f;
+        float best = KNN_INF;
+        int bidx = -1;
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int c = c0 + nt * 8 + 2 * t4 + j;
-                if (c < n)
-                    score[(int64_t)q * stride + c] =
-                        fmaxf(nq2[q] + nc2[c] - 2.f * acc[nt][2 * half + j], 0.f);
+                if (c < n && q < nq) {
+                    const float v = fmaxf(qn + nc2[c] - 2.f * acc[nt][2 * half + j], 0.f);
+                    if (!tile_idx)
+                        score[(int64_t)q * stride + c] = v;
+                    else if (v < best) {
+                        best = v;
+                        bidx = c;
+                    }
+                }
             }
+        if (tile_idx) {
+            // minimum over the 4 lanes that hold this row's 64 columns
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                const float ob = __shfl_xor_sync(KNN_FULL_MASK, best, o);
+                const int oi = __shfl_xor_sync(KNN_FULL_MASK, bidx, o);
+                if (ob < best || (ob == best && oi >= 0 && (bidx < 0 || oi < bidx))) {
+                    best = ob;
+                    bidx = oi;
+                }
+            }
+            if (t4 == 0 && q < nq) {
+                score[(int64_t)q * stride + blockIdx.x] = best;
+                tile_idx[(int64_t)q * stride + blockIdx.x] = bidx;
+            }
+        }
     }
 }
 
@@ -647,11 +672,11 @@ static void enc_backward(knn_encoder *enc, const int *pa, const int *pb, const f
 
 knn_status enc_score(knn_encoder *enc, const __nv_bfloat16 *eq, const float *nq2, int nq,
                      const __nv_bfloat16 *ec, const float *nc2, int n, float *score,
-                     int64_t stride, cudaStream_t st)
+                     int *tile_idx, int64_t stride, cudaStream_t st)
 {
     (void)enc;
     dim3 grid((n + 63) / 64, (nq + 63) / 64);
-    score_kernel<<<grid, 128, 0, st>>>(eq, nq2, nq, ec, nc2, n, score, stride);
+    score_kernel<<<grid, 128, 0, st>>>(eq, nq2, nq, ec, nc2, n, score, tile_idx, stride);
     return KNN_OK;
 }
 
@@ -675,7 +700,7 @@ void enc_init_attributes()
 // series of the database: score[q][c] = ||e_q - e_c||^2 (bucket order).
 knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, const int *q_len,
                            int nq, int max_m, void *qemb_v, float *qnorm, float *scores,
-                           cudaStream_t st)
+                           int *tile_idx, cudaStream_t st)
 {
     __nv_bfloat16 *qemb = static_cast<__nv_bfloat16 *>(qemb_v);
     knn_encoder *enc = db->enc;
@@ -685,7 +710,7 @@ knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, 
         return s;
     enc_emb_bf16(enc->e.as<float>(), nullptr, nq, qemb, qnorm, st);
     return enc_score(enc, qemb, qnorm, nq, db->emb.as<__nv_bfloat16>(), db->emb_norm.as<float>(),
-                     db->N, scores, db->N, st);
+                     db->N, scores, tile_idx, (db->N + 63) / 64, st);
 }
 
 }  // namespace knn

@@ -88,7 +88,8 @@ void launch_greedy(const GreedyArgs &a, int d, int form, cudaStream_t st);
 
 // -- seeded scan: selection of seeds and filtering of survivors -------------
 struct SelArgs {
-    const float *score;        // [nq][score_stride] ranking score per series (bucket order)
+    const float *score;        // [nq][score_stride] ranking score per entry
+    const int *cand;           // nullable: series of each entry (else entry c is series c)
     int64_t score_stride;
     float *lb_all;             // [nq][lb_stride] LB_Box per series; seeds are set to -1
                                // (nullable: feasibility from the lengths, seed bound 0)

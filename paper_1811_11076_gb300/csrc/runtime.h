@@ -92,9 +92,11 @@ struct knn_db;
 namespace knn {
 DpChoice dp_choice(knn_db *db, int kind, int r, int n);
 knn_status enc_work(knn_encoder *enc, int B, int L);
+// Scores of the best series of each 64-series tile per query
+// ([nq][ceil(N/64)], with the series in tile_idx).
 knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, const int *q_len,
                            int nq, int max_m, void *qemb, float *qnorm, float *scores,
-                           cudaStream_t st);
+                           int *tile_idx, cudaStream_t st);
 }
 
 struct knn_db {

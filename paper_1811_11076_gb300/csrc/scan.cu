@@ -14,6 +14,8 @@ using namespace knn;
 
 namespace {
 
+constexpr int DP_GROUPS = 4;  // DP launches per batch at most (length groups)
+
 struct Segment {
     int b_begin, b_end;  // buckets [b_begin, b_end)
     int P, G;
@@ -93,41 +95,39 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
     if (pl.env_stride * 2 * 4 > 200 * 1024)
         return set_error(KNN_ERR_UNSUPPORTED, "envelope larger than shared memory (length x d)");
 
-    // DP segments: consecutive buckets sharing a (P, G) choice
+    // DP segments: at most DP_GROUPS groups of consecutive buckets with
+    // similar series counts, so that every DP launch has enough pairs to
+    // fill the GPU; a group's shape covers its widest band (r of its longest
+    // bucket).  During tuning every bucket is its own segment.
     pl.segs.clear();
     pl.seg_of_bucket.assign(db->buckets.size(), 0);
     int64_t base = 0;
-    for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
-        const Bucket &b = db->buckets[bi];
-        const int r = band_radius(pl.max_m, b.n_hi, p.band);
-        DpChoice c = dp_choice(db, p.distance, r, b.n_hi);
+    const int nb = (int)db->buckets.size();
+    const int groups = db->tuning ? nb : std::min(nb, DP_GROUPS);
+    int64_t per_group = ((int64_t)db->N + groups - 1) / groups;
+    int bi = 0;
+    for (int gi = 0; gi < groups && bi < nb; ++gi) {
+        Segment sg{};
+        sg.b_begin = bi;
+        int64_t cnt = 0;
+        while (bi < nb && (bi == sg.b_begin || cnt < per_group || gi == groups - 1)) {
+            cnt += db->buckets[bi].c_end - db->buckets[bi].c_begin;
+            ++bi;
+            if (db->tuning)
+                break;
+        }
+        sg.b_end = bi;
+        const Bucket &last = db->buckets[bi - 1];
+        const int r = band_radius(pl.max_m, last.n_hi, p.band);
+        DpChoice c = dp_choice(db, p.distance, r, last.n_hi);
         if (c.P == 0)
             return set_error(KNN_ERR_UNSUPPORTED, "band too wide for the compiled DP variants");
-        const int64_t cap = (int64_t)nq * (b.c_end - b.c_begin);
-        if (!pl.segs.empty() && pl.segs.back().P == c.P && pl.segs.back().G == c.G &&
-            !db->tuning) {
-            pl.segs.back().b_end = (int)bi + 1;
-            pl.segs.back().cap += cap;
-        } else if ((int)pl.segs.size() == MAX_SEG) {
-            // out of segments: widen the last one to cover this band too
-            Segment &s = pl.segs.back();
-            s.b_end = (int)bi + 1;
-            s.cap += cap;
-            if (c.G * c.P > s.G * s.P) {
-                s.P = c.P;
-                s.G = c.G;
-            }
-        } else {
-            Segment s;
-            s.b_begin = (int)bi;
-            s.b_end = (int)bi + 1;
-            s.P = c.P;
-            s.G = c.G;
-            s.base = 0;
-            s.cap = cap;
-            pl.segs.push_back(s);
-        }
-        pl.seg_of_bucket[bi] = (int)pl.segs.size() - 1;
+        sg.P = c.P;
+        sg.G = c.G;
+        sg.cap = (int64_t)nq * cnt;
+        for (int b = sg.b_begin; b < sg.b_end; ++b)
+            pl.seg_of_bucket[b] = (int)pl.segs.size();
+        pl.segs.push_back(sg);
     }
     for (auto &s : pl.segs) {
         s.base = base;
@@ -191,7 +191,8 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(out_dist, sizeof(float) * nq * pl.width);
     G_(out_counts, sizeof(int64_t) * nq);
     if (pl.seeded && p_learned(pl)) {
-        G_(scores, sizeof(float) * nq * (size_t)db->N);
+        G_(scores, sizeof(float) * nq * (size_t)((db->N + 63) / 64));
+        G_(sel, sizeof(int) * nq * (size_t)((db->N + 63) / 64));
         G_(skip, sizeof(uint32_t) * nq * (size_t)((db->N + 31) / 32));
         G_(qemb, sizeof(uint16_t) * nq * 64);
         G_(qnorm, sizeof(float) * nq);
@@ -310,14 +311,17 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     // against the seeded threshold directly
     if (pl.learned) {
         enc_scan_scores(db, ws.qbuf.as<float>(), ws.q_off.as<int64_t>(), ws.q_len.as<int>(), nq,
-                        pl.max_m, ws.qemb.p, ws.qnorm.as<float>(), ws.scores.as<float>(), st);
+                        pl.max_m, ws.qemb.p, ws.qnorm.as<float>(), ws.scores.as<float>(),
+                        ws.sel.as<int>(), st);
+        const int tiles = (db->N + 63) / 64;
         SelArgs sa{};
         sa.score = ws.scores.as<float>();
-        sa.score_stride = db->N;
+        sa.cand = ws.sel.as<int>();
+        sa.score_stride = tiles;
         sa.q_len = ws.q_len.as<int>();
         sa.db_len = db->len.as<int>();
         sa.band = p.band;
-        sa.n = db->N;
+        sa.n = tiles;
         sa.nq = nq;
         sa.S = pl.S;
         sa.seed_items = ws.seed_items.as<int2>();

@@ -24,13 +24,18 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
     __shared__ int s_bin, s_before, s_taken, s_count;
     const int q = blockIdx.x;
     const float *score = a.score + (int64_t)q * a.score_stride;
+    const int *cand = a.cand ? a.cand + (int64_t)q * a.score_stride : nullptr;
     float *lb = a.lb_all ? a.lb_all + (int64_t)q * a.lb_stride : nullptr;
     const int m = a.lb_all ? 0 : a.q_len[q];
     // a series can be a seed if its end cell is inside the band
+    auto series = [&](int c) -> int { return cand ? cand[c] : a.c_base + c; };
     auto feasible = [&](int c) -> bool {
         if (lb)
             return lb[c] < KNN_INF;
-        const int n = a.db_len[a.c_base + c];
+        const int sidx = series(c);
+        if (sidx < 0)
+            return false;
+        const int n = a.db_len[sidx];
         return abs(m - n) <= band_radius(m, n, a.band);
     };
     for (int i = threadIdx.x; i < SEL_BINS; i += blockDim.x)
@@ -70,13 +75,14 @@ __global__ void __launch_bounds__(SEL_THREADS) select_kernel(const SelArgs a)
         if (take) {
             const int pos = atomicAdd(a.n_seed, 1);
             if (pos < a.seed_cap) {
-                a.seed_items[pos] = make_int2(a.c_base + c, q);
+                const int sidx = series(c);
+                a.seed_items[pos] = make_int2(sidx, q);
                 a.seed_lb[pos] = lb ? lb[c] : 0.f;
                 if (lb)
                     lb[c] = -1.f;  // scored as a seed; the filter skips it
                 if (a.seed_bits)   // scored as a seed; the LB_Box stream skips it
-                    atomicOr(a.seed_bits + (int64_t)q * a.bits_words + ((a.c_base + c) >> 5),
-                             1u << ((a.c_base + c) & 31));
+                    atomicOr(a.seed_bits + (int64_t)q * a.bits_words + (sidx >> 5),
+                             1u << (sidx & 31));
                 atomicAdd(&s_count, 1);
             } else {
                 atomicOr(a.status, KNN_DEV_CAPACITY);
