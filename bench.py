@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -54,6 +55,13 @@ SEED_DESC = {"greedy": "greedy upper-bound pre-pass over every series (Section 4
                         "LB_Box stream with early abandoning",
              "none": "no seeding"}
 TRAIN_PAIRS = 200_000
+
+
+# DRAM bytes (read + write) per launch of the dominant kernels on the bench
+# workloads, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
+# captures of the current kernels (the summaries in profiles/ give the commands).
+# A kernel changed since its capture has no entry (traffic null).
+TRAFFIC = {}
 
 
 def peaks():
@@ -315,37 +323,51 @@ def run_gpu(args):
         }
     launches = sum(s["launches"] for _, s in collected)
 
-    # roofline of the dominant kernel (largest share of stage time)
+    # roofline of the dominant kernel (largest share of stage time).  Both
+    # stages are plain FP32-ALU work: the LB_Box stream with a tile of queries
+    # per pass does 4 lane operations per (query, element) it evaluates (max,
+    # min, sub, FMA; the DK max form adds one max per point), the DP 2d+3 per
+    # band cell.  Peak = SMs x 128 FP32 lanes x the maximum SM clock.
     hbm_gbs, sm_max_mhz, peak_src = peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
     stage = {"seed": 0.0, "lb": 0.0, "dp": 0.0, "finalize": 0.0}
-    cells = {kind: 0 for kind in kinds}
-    lb_bytes = 0
+    dp_ops = lb_ops = 0.0
+    lb_launches = dp_launches = 0
     for kind, s in collected:
         for k_ in stage:
             stage[k_] += s[f"ms_{k_}"]
-        cells[kind] += s["dp_cells"]
-        lb_bytes += s["lb_points"] * D * 4
-    dominant = max(stage, key=stage.get)
+        dp_ops += s["dp_cells"] * (2 * D + 3)
+        lb_ops += s["lb_points"] * (4 * D + (1 if kind == kw.DK else 0))
     clocks = clk.summary()
-    if dominant == "lb":
-        achieved = lb_bytes / (stage["lb"] / 1000.0) / 1e9
-        roof = {"kernel": "lb_kernel", "bound": "hbm", "achieved": achieved, "peak": hbm_gbs,
-                "unit": "GB/s", "frac": achieved / hbm_gbs, "traffic": None,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        # algorithmic work of the DP: 2d+3 FP32 lane operations per band cell
-        ops = sum(cells.values()) * (2 * D + 3)
-        achieved = ops / (stage["dp"] / 1000.0) / 1e12
-        peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
-        roof = {"kernel": "dp_kernel" if dominant == "dp" else dominant, "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "Tops/s (FP32 lane ops)",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
-                               f"(max SM clock, {peak_src})",
-                "stage_share": {k_: v / sum(stage.values()) for k_, v in stage.items()}}
+    share = {k_: v / max(sum(stage.values()), 1e-12) for k_, v in stage.items()}
+
+    def alu_roof(kernel, ops, ms_):
+        achieved = ops / (ms_ / 1000.0) / 1e12 if ms_ else 0.0
+        r_ = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+              "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
+              "traffic": TRAFFIC.get((kernel, WORKLOAD)),
+              "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
+                             f"(max SM clock, {peak_src})"}
         if clocks.get("sm_mhz"):
-            roof["frac_at_sampled_clock"] = achieved / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+            r_["frac_at_sampled_clock"] = achieved / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+        return r_
+
+    # the library stages a tile's whole envelopes when 16 of them fit in
+    # 192 KB of shared memory (lb_multi_kernel), else windows (lb_win_kernel)
+    deff = D if D <= 8 else 16
+    ch = deff * 4 // math.gcd(deff, 4)
+    longest = LENGTH or int(np.diff(w.db_off).max())
+    shortest = LENGTH or int(np.diff(w.db_off).min())
+    env_bytes = [-(-n_ // (ch // deff)) * ch * 8 * 16 for n_ in (shortest, longest)]
+    lb_name = ("lb_multi_kernel" if env_bytes[1] <= 192 * 1024 else
+               "lb_win_kernel" if env_bytes[0] > 192 * 1024 else "lb_multi_kernel+lb_win_kernel")
+    stage_roofs = {"lb": alu_roof(lb_name, lb_ops, stage["lb"]),
+                   "dp": alu_roof("dp_kernel", dp_ops, stage["dp"])}
+    dominant = "lb" if stage["lb"] >= stage["dp"] else "dp"
+    roof = dict(stage_roofs[dominant])
+    roof["stage_share"] = share
+    roof["other_stage"] = stage_roofs["dp" if dominant == "lb" else "lb"]
 
     # end to end through the public API with host buffers: H2D of queries and
     # D2H of results inside the timed region

@@ -178,7 +178,10 @@ KNN_API knn_status knn_scan_simple(const float *query, int64_t m, const float *d
 /* pair and P band diagonals to each lane (2P cells per lane per two        */
 /* anti-diagonals); G*P >= r+1 must hold.  A shape is chosen per            */
 /* (distance, r, n) key, r the band radius and n the longest series of a    */
-/* length bucket.  Without tuning, a cost model picks it.                   */
+/* length bucket.  Without tuning, a cost model picks it.  The widest band  */
+/* is r <= 32 * P_max - 1 with P_max the largest compiled P: r <= 415 for   */
+/* d <= 3, 223 for d = 4..6, 127 for d = 7, 8 and 9..16; wider bands return  */
+/* KNN_ERR_UNSUPPORTED.                                                     */
 
 /* Time every compiled shape for each length bucket on the given queries
  * (one full scan per shape, each bucket's DP launch timed with CUDA events)
@@ -199,6 +202,20 @@ KNN_API knn_status knn_get_dp_shape(knn_db *db, int32_t distance, int32_t r, int
 /* Compiled P values for dimensionality d: writes up to cap of them to
  * P_list (nullable) and returns how many exist. */
 KNN_API int32_t knn_dp_shapes(int32_t d, int32_t *P_list, int32_t cap);
+
+/* Query tile of the LB_Box stream (Section 3, Eq. 1) for one distance: a
+ * CTA bounds its 256 series against qtile queries at once (4, 8 or 16; 0 =
+ * 16, or the tuned value) so that the database is read once per tile.
+ * window_chunks = 0: a CTA stages the tile's whole envelopes in shared
+ * memory when they fit (2 * 4 * qtile * padded length * d bytes <= 192 KB)
+ * and windows of them otherwise; > 0: always windows of that many chunks of
+ * lcm(d', 4) floats (clamped to what fits).  The result of a scan does not
+ * depend on either value.  KNN_ERR_INVALID for other qtile values or a
+ * negative window. */
+KNN_API knn_status knn_set_lb_tile(knn_db *db, int32_t distance, int32_t qtile,
+                                   int32_t window_chunks);
+KNN_API knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qtile,
+                                   int32_t *window_chunks);
 
 /* ---------------------------------------------------------------------- */
 /* Components (each is one step of the scan, exposed for verification and  */

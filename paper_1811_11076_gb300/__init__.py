@@ -38,7 +38,7 @@ STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA"
 EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
-           "knn_dp_shapes", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
+           "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
            "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach",
            "knn_encoder_params", "knn_encoder_loss_grad", "knn_encoder_save", "knn_encoder_load")
 
@@ -112,6 +112,8 @@ def lib() -> C.CDLL:
     L.knn_set_dp_shape.argtypes = [vp] + [C.c_int32] * 5
     L.knn_get_dp_shape.argtypes = [vp] + [C.c_int32] * 3 + [C.POINTER(C.c_int32)] * 2
     L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
+    L.knn_set_lb_tile.argtypes = [vp] + [C.c_int32] * 3
+    L.knn_get_lb_tile.argtypes = [vp, C.c_int32] + [C.POINTER(C.c_int32)] * 2
     L.knn_pairwise_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp, C.c_int64,
                                        C.c_int32, C.c_float, C.c_int32, C.c_int32, vp, vp]
     L.knn_encoder_num_params.restype = C.c_int32
@@ -262,6 +264,15 @@ class KnnDB:
 
     def set_dp_shape(self, distance: int, r: int, n: int, P: int, G: int):
         _check(lib().knn_set_dp_shape(self._h, distance, r, n, P, G))
+
+    def set_lb_tile(self, distance: int, qtile: int = 0, window_chunks: int = 0):
+        """Queries per LB_Box pass and the envelope window (0: automatic)."""
+        _check(lib().knn_set_lb_tile(self._h, distance, qtile, window_chunks))
+
+    def get_lb_tile(self, distance: int):
+        q, w = C.c_int32(), C.c_int32()
+        _check(lib().knn_get_lb_tile(self._h, distance, C.byref(q), C.byref(w)))
+        return q.value, w.value
 
     def get_dp_shape(self, distance: int, r: int, n: int):
         P, G = C.c_int32(), C.c_int32()

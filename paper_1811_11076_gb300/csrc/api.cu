@@ -131,6 +131,22 @@ static int next_pow2(int v)
 
 // Default (P, G) for a band radius r: minimise the modelled lane work
 // G * (n + P + 1) * (2P(2d+3) + overhead) subject to G*P >= r+1, G <= 32.
+namespace {
+// Resident CTAs per SM of the DTW variant (d, P), looked up once.
+int dp_blocks_cached(int deff, int P)
+{
+    static int cache[17][33];
+    static bool filled[17][33];
+    if (deff < 1 || deff > 16 || P < 1 || P > 32)
+        return 1;
+    if (!filled[deff][P]) {
+        cache[deff][P] = knn::dp_max_blocks_per_sm(deff, P, 0);
+        filled[deff][P] = true;
+    }
+    return cache[deff][P] > 0 ? cache[deff][P] : 1;
+}
+}  // namespace
+
 void knn::choose_dp_config(int deff, int r, int n, int *P_out, int *G_out)
 {
     double best = 1e300;
@@ -144,7 +160,10 @@ void knn::choose_dp_config(int deff, int r, int n, int *P_out, int *G_out)
         if (G > 32)
             continue;
         const double per_step = 2.0 * P * (2 * deff + 3) + 16.0 + 2.0 * deff;
-        const double cost = (double)G * (n + P + 1) * per_step;
+        // fewer than 16 resident warps per SM leave latency uncovered: the
+        // kernel then runs at about that fraction of its issue rate
+        const double warps = (double)dp_blocks_cached(deff, P) * dp_block_threads() / 32.0;
+        const double cost = (double)G * (n + P + 1) * per_step / std::min(1.0, std::max(warps, 1.0) / 16.0);
         if (cost < best) {
             best = cost;
             bp = P;

@@ -273,6 +273,34 @@ extern "C" knn_status knn_get_dp_shape(knn_db *db, int32_t distance, int32_t r, 
     return c.P ? KNN_OK : set_error(KNN_ERR_UNSUPPORTED, "no compiled shape covers the band");
 }
 
+extern "C" knn_status knn_set_lb_tile(knn_db *db, int32_t distance, int32_t qtile,
+                                      int32_t window_chunks)
+{
+    if (!db)
+        return set_error(KNN_ERR_INVALID, "db is NULL");
+    if (distance != KNN_DTW && distance != KNN_DK)
+        return set_error(KNN_ERR_INVALID, "distance must be KNN_DTW or KNN_DK");
+    if (qtile != 0 && qtile != 4 && qtile != 8 && qtile != 16)
+        return set_error(KNN_ERR_INVALID, "qtile must be 0, 4, 8 or 16");
+    if (window_chunks < 0)
+        return set_error(KNN_ERR_INVALID, "window_chunks must be >= 0");
+    db->lb_qtile[distance] = qtile;
+    db->lb_window[distance] = window_chunks;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qtile,
+                                      int32_t *window_chunks)
+{
+    if (!db || !qtile || !window_chunks)
+        return set_error(KNN_ERR_INVALID, "NULL argument");
+    if (distance != KNN_DTW && distance != KNN_DK)
+        return set_error(KNN_ERR_INVALID, "distance must be KNN_DTW or KNN_DK");
+    *qtile = db->lb_qtile[distance];
+    *window_chunks = db->lb_window[distance];
+    return KNN_OK;
+}
+
 extern "C" int32_t knn_dp_shapes(int32_t d, int32_t *P_list, int32_t cap)
 {
     const int deff = deff_for(d);

@@ -63,6 +63,31 @@ __device__ __forceinline__ float fmin3(float a, float b, float c)
     return d;
 }
 
+// max(a, b, c) in one instruction (three-input PTX max, sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Distance of x to the interval [l, u] (l <= u, or l = +inf / u = -inf for
+// an empty window): the positive one of l - x and x - u, else 0.  Equal to
+// x - clamp(x, l, u) in magnitude bit for bit (the same single rounded
+// subtraction), with one three-input max instead of a max and a min.
+__device__ __forceinline__ float box_gap(float x, float l, float u)
+{
+    return fmax3(l - x, x - u, 0.f);
+}
+
+// a - b on both lanes of a packed pair, one rounding each (b * -1 is exact,
+// so the fused form rounds exactly like a subtraction).  Packed FP32 pairs
+// (sm_100 and later) halve the instructions issued per coordinate.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 // Squared Euclidean distance, accumulated on top of `init` with FMAs in
 // coordinate order.  init = +inf masks a cell out of the band.
 template <int D>
@@ -71,7 +96,7 @@ __device__ __forceinline__ float sqdist_acc(const float (&a)[D], const float (&b
     float acc = init;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        float t = a[k] - b[k];
+        const float t = a[k] - b[k];
         acc = __fmaf_rn(t, t, acc);
     }
     return acc;

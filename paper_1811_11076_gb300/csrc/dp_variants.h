@@ -12,4 +12,4 @@
     X(6, 2) X(6, 4) X(6, 7)                                                        \
     X(7, 2) X(7, 4)                                                                \
     X(8, 2) X(8, 4)                                                                \
-    X(16, 2)
+    X(16, 2) X(16, 4)

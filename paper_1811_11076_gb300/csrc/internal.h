@@ -60,7 +60,9 @@ struct LbArgs {
     unsigned long long *stats; // [STAT_*]
     int *status;
     int single_query_kernel;   // 1: always the warp-per-series kernel
-    int qtile;                 // queries per CTA of the multi-query kernel (0: largest fitting)
+    int qtile;                 // queries per CTA of the multi-query kernel (0: 16)
+    int win_chunks;            // > 0: windowed multi-query kernel with windows of this many
+                               // chunks; 0: whole envelopes when they fit, else windowed
 };
 void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();

@@ -132,8 +132,7 @@ __device__ __forceinline__ void lb_chunk(const float4 (&xv)[F4], const float4 *l
         float box = 0.f;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const float x = v[p * D + k];
-            const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
+            const float e = box_gap(v[p * D + k], l[p * D + k], u[p * D + k]);
             box = __fmaf_rn(e, e, box);
         }
         if (ch * PPC + p < n)
@@ -273,17 +272,197 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Multi-query LB_Box kernel: grid (x: blocks of 256 series, y: query tiles).
+// Multi-query LB_Box kernels: grid (x: blocks of 256 series, y: query tiles).
 //
 // One thread owns one series and QT queries: it loads a chunk of its series
-// once and bounds it against the QT query envelopes, which the CTA staged in
-// shared memory with one TMA bulk copy per array; when the series of a warp
-// have the same length every lane reads the same envelope address (a
-// broadcast).  So the database is read once per QT queries and each element
-// costs 4 FP32 operations per query (max, min, sub, fma).
+// once and bounds it against the QT query envelopes held in shared memory;
+// when the series of a warp have the same length every lane reads the same
+// envelope address (a broadcast).  So the database is read once per QT
+// queries and each element costs 4 FP32 operations per query (two
+// subtractions, a three-input max, an FMA).
 
+// Bound one chunk of a thread's series against QT envelopes: lo/hi point at
+// the chunk's envelope of the tile's first query, the next query's lies
+// qstride4 float4 further.  p_first = index of the chunk's first point.
+// The subtractions and squares run on packed FP32 pairs; a chunk's squares
+// are summed on their own before joining the series' total, so a bound of n
+// points carries at most CH/2 + 2 + n roundings in the sum form (d in the
+// max form).
 template <int D, int FORM, int QT>
-__global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
+__device__ __forceinline__ void lb_multi_chunk(const float4 *__restrict__ x4c, const float4 *lo,
+                                               const float4 *hi, int qstride4, bool full,
+                                               int p_first, int n, float (&acc)[QT])
+{
+    constexpr int CH = chunk_floats(D);
+    constexpr int PPC = chunk_points(D);
+    constexpr int F4 = CH / 4;
+    float4 xv[F4];
+#pragma unroll
+    for (int f = 0; f < F4; ++f)
+        xv[f] = __ldg(x4c + f);
+#pragma unroll
+    for (int j = 0; j < QT; ++j) {
+        // e = distance of every element to its box, max(l - x, x - u, 0)
+        float e[CH];
+#pragma unroll
+        for (int f = 0; f < F4; ++f) {
+            const float4 lv = lo[j * qstride4 + f];
+            const float4 uv = hi[j * qstride4 + f];
+            const float2 x01 = make_float2(xv[f].x, xv[f].y), x23 = make_float2(xv[f].z, xv[f].w);
+            const float2 a01 = sub2(make_float2(lv.x, lv.y), x01);
+            const float2 a23 = sub2(make_float2(lv.z, lv.w), x23);
+            const float2 b01 = sub2(x01, make_float2(uv.x, uv.y));
+            const float2 b23 = sub2(x23, make_float2(uv.z, uv.w));
+            e[4 * f] = fmax3(a01.x, b01.x, 0.f);
+            e[4 * f + 1] = fmax3(a01.y, b01.y, 0.f);
+            e[4 * f + 2] = fmax3(a23.x, b23.x, 0.f);
+            e[4 * f + 3] = fmax3(a23.y, b23.y, 0.f);
+        }
+        if (full && FORM == 0) {
+            // whole chunk inside the series: no per-point test
+            float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < CH; i += 2) {
+                const float2 t = make_float2(e[i], e[i + 1]);
+                s = __ffma2_rn(t, t, s);
+            }
+            acc[j] += s.x + s.y;
+        } else if constexpr (D % 2 == 0) {
+            // points hold whole pairs
+#pragma unroll
+            for (int p = 0; p < PPC; ++p) {
+                float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < D; k += 2) {
+                    const float2 t = make_float2(e[p * D + k], e[p * D + k + 1]);
+                    s = __ffma2_rn(t, t, s);
+                }
+                const float box = s.x + s.y;
+                if (full || p_first + p < n)
+                    acc[j] = FORM == 0 ? acc[j] + box : fmaxf(acc[j], box);
+            }
+        } else {
+            float sq[CH];
+#pragma unroll
+            for (int i = 0; i < CH; i += 2) {
+                const float2 t = make_float2(e[i], e[i + 1]);
+                const float2 q2 = __fmul2_rn(t, t);
+                sq[i] = q2.x;
+                sq[i + 1] = q2.y;
+            }
+#pragma unroll
+            for (int p = 0; p < PPC; ++p) {
+                float box = sq[p * D];
+#pragma unroll
+                for (int k = 1; k < D; ++k)
+                    box += sq[p * D + k];
+                if (full || p_first + p < n)
+                    acc[j] = FORM == 0 ? acc[j] + box : fmaxf(acc[j], box);
+            }
+        }
+    }
+}
+
+template <int QT>
+__device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float (&lim)[QT])
+{
+    bool all_over = true;
+#pragma unroll
+    for (int j = 0; j < QT; ++j)
+        all_over &= acc[j] > lim[j];
+    return all_over;
+}
+
+// Per-thread set-up shared by the multi-query kernels: query lengths and the
+// pruning limits of the tile (filter mode; -1 for missing queries so that
+// they never hold a series back).
+template <int QT>
+__device__ __forceinline__ void lb_multi_setup(const LbArgs &a, int q0, int nqt, int (&mq)[QT],
+                                               float (&lim)[QT])
+{
+#pragma unroll
+    for (int j = 0; j < QT; ++j) {
+        mq[j] = j < nqt ? a.q_len[q0 + j] : 1;
+        lim[j] = (a.items && j < nqt) ? ld_volatile_f32(a.thr + q0 + j) * a.mu_prune : KNN_INF;
+        if (j >= nqt)
+            lim[j] = -1.f;
+    }
+}
+
+// Results of one series against the tile: bound output (store mode) or the
+// survivor queue (filter mode), and the counters.  Warp-converged.
+template <int QT>
+__device__ __forceinline__ void lb_multi_finish(const LbArgs &a, int q0, int nqt,
+                                                const int (&mq)[QT], const float (&lim)[QT],
+                                                const float (&acc)[QT], bool valid, int c, int n,
+                                                int lane, unsigned long long &st_pairs,
+                                                unsigned long long &st_inf,
+                                                unsigned long long &st_pruned)
+{
+#pragma unroll
+    for (int j = 0; j < QT; ++j) {
+        if (j >= nqt)
+            break;
+        const int qb = q0 + j;
+        const int r = band_radius(mq[j], n, a.band);
+        const bool feasible = valid && abs(mq[j] - n) <= r;
+        const float lb = feasible ? acc[j] : KNN_INF;
+        if (valid && a.out_lb)
+            a.out_lb[(int64_t)qb * a.out_lb_stride + c] = lb;
+        st_pairs += valid;
+        st_inf += valid && !feasible;
+        if (a.items) {
+            bool seeded = false;
+            if (a.skip && valid)
+                seeded = (a.skip[(int64_t)qb * a.skip_words + (c >> 5)] >> (c & 31)) & 1u;
+            const bool keep = feasible && !seeded && lb <= lim[j];
+            // proposals already scored count as pruned: they are not queued again
+            st_pruned += feasible && !keep;
+            const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
+            if (kb) {
+                int base = 0;
+                if (lane == 0)
+                    base = atomicAdd(a.n_items, __popc(kb));
+                base = __shfl_sync(KNN_FULL_MASK, base, 0);
+                if (keep) {
+                    const int64_t pos = (int64_t)base + __popc(kb & ((1u << lane) - 1u));
+                    if (pos < a.capacity) {
+                        a.items[pos] = make_int2(c, qb);
+                        a.item_lb[pos] = lb;
+                    } else {
+                        atomicOr(a.status, KNN_DEV_CAPACITY);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void lb_flush_stats(const LbArgs &a, int lane, unsigned long long st_pairs,
+                                               unsigned long long st_inf,
+                                               unsigned long long st_pruned,
+                                               unsigned long long st_points)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st_pairs += __shfl_xor_sync(KNN_FULL_MASK, st_pairs, o);
+        st_inf += __shfl_xor_sync(KNN_FULL_MASK, st_inf, o);
+        st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
+        st_points += __shfl_xor_sync(KNN_FULL_MASK, st_points, o);
+    }
+    if (lane == 0 && a.stats) {
+        atomicAdd(a.stats + STAT_PAIRS, st_pairs);
+        atomicAdd(a.stats + STAT_INFEASIBLE, st_inf);
+        atomicAdd(a.stats + STAT_LB_PRUNED, st_pruned);
+        atomicAdd(a.stats + STAT_LB_POINTS, st_points);
+    }
+}
+
+// Whole envelopes: the CTA stages its QT envelopes of this bucket once
+// (one TMA bulk copy per array and query) and walks several 256-series
+// batches.
+template <int D, int FORM, int QT>
+__global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
 {
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
@@ -321,13 +500,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
 
     int mq[QT];
     float lim[QT];  // filter mode: a series is done once every bound exceeds its limit
-#pragma unroll
-    for (int j = 0; j < QT; ++j) {
-        mq[j] = j < nqt ? a.q_len[q0 + j] : 1;
-        lim[j] = (a.items && j < nqt) ? ld_volatile_f32(a.thr + q0 + j) * a.mu_prune : KNN_INF;
-        if (j >= nqt)
-            lim[j] = -1.f;
-    }
+    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
     unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
     const int nser = a.c_end - a.c_begin;
     const int span = (nser + LB_THREADS - 1) / LB_THREADS * LB_THREADS;
@@ -342,124 +515,148 @@ __global__ void __launch_bounds__(LB_THREADS) lb_multi_kernel(const LbArgs a)
         const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
         const int nch = (n + PPC - 1) / PPC;
         for (int ch = 0; ch < nch; ++ch) {
-            if (a.items && (ch & 3) == 0) {
-                // early abandoning of the bound (Section 4): partial sums and
-                // maxima only grow, so once all exceed their limits the series
-                // is pruned for every query of the tile
-                bool all_over = true;
-#pragma unroll
-                for (int j = 0; j < QT; ++j)
-                    all_over &= acc[j] > lim[j];
-                if (all_over)
-                    break;
-            }
-            const bool full = (ch + 1) * PPC <= n;
-            st_points += (unsigned long long)PPC * nqt;
-            float v[CH];
-#pragma unroll
-            for (int f = 0; f < F4; ++f) {
-                const float4 t = __ldg(x4 + ch * F4 + f);
-                v[4 * f] = t.x; v[4 * f + 1] = t.y; v[4 * f + 2] = t.z; v[4 * f + 3] = t.w;
-            }
-#pragma unroll
-            for (int j = 0; j < QT; ++j) {
-                float l[CH], u[CH];
-#pragma unroll
-                for (int f = 0; f < F4; ++f) {
-                    const float4 lv = lo_s[j * st4 + ch * F4 + f];
-                    const float4 uv = hi_s[j * st4 + ch * F4 + f];
-                    l[4 * f] = lv.x; l[4 * f + 1] = lv.y; l[4 * f + 2] = lv.z; l[4 * f + 3] = lv.w;
-                    u[4 * f] = uv.x; u[4 * f + 1] = uv.y; u[4 * f + 2] = uv.z; u[4 * f + 3] = uv.w;
-                }
-                if (full) {
-                    // whole chunk inside the series: no per-point test
-                    if (FORM == 0) {
-                        float sacc = acc[j];
-#pragma unroll
-                        for (int e2 = 0; e2 < CH; ++e2) {
-                            const float e = v[e2] - fminf(fmaxf(v[e2], l[e2]), u[e2]);
-                            sacc = __fmaf_rn(e, e, sacc);
-                        }
-                        acc[j] = sacc;
-                    } else {
-#pragma unroll
-                        for (int p = 0; p < PPC; ++p) {
-                            float box = 0.f;
-#pragma unroll
-                            for (int k = 0; k < D; ++k) {
-                                const float x = v[p * D + k];
-                                const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
-                                box = __fmaf_rn(e, e, box);
-                            }
-                            acc[j] = fmaxf(acc[j], box);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int p = 0; p < PPC; ++p) {
-                        float box = 0.f;
-#pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            const float x = v[p * D + k];
-                            const float e = x - fminf(fmaxf(x, l[p * D + k]), u[p * D + k]);
-                            box = __fmaf_rn(e, e, box);
-                        }
-                        if (ch * PPC + p < n)
-                            acc[j] = FORM == 0 ? acc[j] + box : fmaxf(acc[j], box);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < QT; ++j) {
-            if (j >= nqt)
+            // early abandoning of the bound (Section 4): partial sums and
+            // maxima only grow, so once all exceed their limits the series
+            // is pruned for every query of the tile
+            if (a.items && (ch & 3) == 0 && lb_all_over<QT>(acc, lim))
                 break;
-            const int qb = q0 + j;
-            const int r = band_radius(mq[j], n, a.band);
-            const bool feasible = valid && abs(mq[j] - n) <= r;
-            const float lb = feasible ? acc[j] : KNN_INF;
-            if (valid && a.out_lb)
-                a.out_lb[(int64_t)qb * a.out_lb_stride + c] = lb;
-            st_pairs += valid;
-            st_inf += valid && !feasible;
-            if (a.items) {
-                bool seeded = false;
-                if (a.skip && valid)
-                    seeded = (a.skip[(int64_t)qb * a.skip_words + (c >> 5)] >> (c & 31)) & 1u;
-                const bool keep = feasible && !seeded && lb <= lim[j];
-                st_pruned += feasible && !keep;
-                const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
-                if (kb) {
-                    int base = 0;
-                    if (lane == 0)
-                        base = atomicAdd(a.n_items, __popc(kb));
-                    base = __shfl_sync(KNN_FULL_MASK, base, 0);
-                    if (keep) {
-                        const int64_t pos = (int64_t)base + __popc(kb & ((1u << lane) - 1u));
-                        if (pos < a.capacity) {
-                            a.items[pos] = make_int2(c, qb);
-                            a.item_lb[pos] = lb;
-                        } else {
-                            atomicOr(a.status, KNN_DEV_CAPACITY);
-                        }
-                    }
-                }
-            }
+            st_points += (unsigned long long)PPC * nqt;
+            lb_multi_chunk<D, FORM, QT>(x4 + ch * F4, lo_s + ch * F4, hi_s + ch * F4, st4,
+                                        (ch + 1) * PPC <= n, ch * PPC, n, acc);
         }
+        lb_multi_finish<QT>(a, q0, nqt, mq, lim, acc, valid, c, n, lane, st_pairs, st_inf,
+                            st_pruned);
     }
+    lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
+}
+
+// Bounded wait for the given phase parity of an mbarrier.
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < KNN_SPIN_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (it > 64)
+            __nanosleep(256);
+    }
+    return false;
+}
+
+// Windowed envelopes, for envelopes too large to stage whole (long series,
+// high d): the CTA owns one batch of 256 series and walks the bucket's
+// chunks in windows of a.win_chunks; the QT envelopes of each window are
+// brought in by TMA bulk copies into one of two buffers while the other is
+// being read.  Between windows the CTA votes: once every series of the batch
+// exceeds its limits for every query (filter mode), the rest is skipped.
+template <int D, int FORM, int QT>
+__global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
+{
+    constexpr int CH = chunk_floats(D);
+    constexpr int PPC = chunk_points(D);
+    constexpr int F4 = CH / 4;
+    // two buffers, each [QT][win] lo then [QT][win] hi (float4 units)
+    extern __shared__ __align__(128) float4 env_s[];
+    __shared__ __align__(8) uint64_t bar[2];
+
+    const int WCH = a.win_chunks;
+    const int wst4 = WCH * F4;
+    const int buf4 = 2 * QT * wst4;
+    const int q0 = blockIdx.y * QT;
+    const int nqt = min(QT, a.nq - q0);
+    const int lane = threadIdx.x & 31;
+    const int nch_env = a.env_floats / CH;
+    const int W = (nch_env + WCH - 1) / WCH;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // window w goes to buffer w & 1; it is that barrier's (w >> 1)-th phase
+    auto issue = [&](int w) {
+        const int c0 = w * WCH;
+        const int cnt = min(WCH, nch_env - c0);
+        const uint32_t bytes = (uint32_t)cnt * CH * 4u;
+        float4 *dst = env_s + (w & 1) * buf4;
+        mbar_expect_tx(&bar[w & 1], 2u * bytes * (uint32_t)nqt);
+        for (int j = 0; j < nqt; ++j) {
+            const int64_t src = (int64_t)(q0 + j) * a.env_stride + (int64_t)c0 * CH;
+            tma_bulk_g2s(dst + j * wst4, a.env_lo + src, bytes, &bar[w & 1]);
+            tma_bulk_g2s(dst + (QT + j) * wst4, a.env_hi + src, bytes, &bar[w & 1]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        issue(0);
+        if (W > 1)
+            issue(1);
+    }
+
+    int mq[QT];
+    float lim[QT];
+    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
+    const int nser = a.c_end - a.c_begin;
+    const int i = blockIdx.x * LB_THREADS + threadIdx.x;
+    const bool valid = i < nser;
+    const int c = a.c_begin + (valid ? i : 0);
+    const int n = valid ? a.db_len[c] : 0;
+    const int nch = (n + PPC - 1) / PPC;
+    const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+    float acc[QT];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        st_pairs += __shfl_xor_sync(KNN_FULL_MASK, st_pairs, o);
-        st_inf += __shfl_xor_sync(KNN_FULL_MASK, st_inf, o);
-        st_pruned += __shfl_xor_sync(KNN_FULL_MASK, st_pruned, o);
-        st_points += __shfl_xor_sync(KNN_FULL_MASK, st_points, o);
+    for (int j = 0; j < QT; ++j)
+        acc[j] = 0.f;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
+
+    int w = 0;
+    bool failed = false;
+    for (; w < W; ++w) {
+        const bool ok = mbar_wait_parity(&bar[w & 1], (uint32_t)(w >> 1) & 1u);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const float4 *lo_w = env_s + (w & 1) * buf4;
+        const float4 *hi_w = lo_w + QT * wst4;
+        const int cb = w * WCH;
+        const int ce = min(cb + WCH, nch);
+        for (int ch = cb; ch < ce; ++ch) {
+            if (a.items && ((ch - cb) & 3) == 0 && lb_all_over<QT>(acc, lim))
+                break;
+            st_points += (unsigned long long)PPC * nqt;
+            lb_multi_chunk<D, FORM, QT>(x4 + ch * F4, lo_w + (ch - cb) * F4, hi_w + (ch - cb) * F4,
+                                        wst4, (ch + 1) * PPC <= n, ch * PPC, n, acc);
+        }
+        const bool finished = nch <= cb + WCH || (a.items && lb_all_over<QT>(acc, lim));
+        // every thread is done with buffer w & 1 after this barrier
+        const bool all_finished = __syncthreads_and(finished);
+        if (all_finished)
+            break;
+        if (threadIdx.x == 0 && w + 2 < W)
+            issue(w + 2);
     }
-    if (lane == 0 && a.stats) {
-        atomicAdd(a.stats + STAT_PAIRS, st_pairs);
-        atomicAdd(a.stats + STAT_INFEASIBLE, st_inf);
-        atomicAdd(a.stats + STAT_LB_PRUNED, st_pruned);
-        atomicAdd(a.stats + STAT_LB_POINTS, st_points);
+    // copies still in flight into this CTA's shared memory end before it exits
+    if (threadIdx.x == 0) {
+        // issued: windows [0, min(W, w + 2)); waited for: [0, w) or [0, w]
+        const int first = failed ? w : w + 1;
+        for (int v = first; v < min(W, w + 2); ++v)
+            mbar_wait_parity(&bar[v & 1], (uint32_t)(v >> 1) & 1u);
     }
+    if (failed) {
+        if (lane == 0)
+            atomicOr(a.status, KNN_DEV_TIMEOUT);
+        return;
+    }
+    lb_multi_finish<QT>(a, q0, nqt, mq, lim, acc, valid, c, n, lane, st_pairs, st_inf, st_pruned);
+    lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
 }
 
 template <int D, int QT>
@@ -468,6 +665,10 @@ static void lb_attr_q()
     cudaFuncSetAttribute(lb_multi_kernel<D, 0, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(lb_multi_kernel<D, 1, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(lb_win_kernel<D, 0, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(lb_win_kernel<D, 1, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
 }
 
@@ -505,20 +706,49 @@ static void lb_multi_launch(const LbArgs &a, int form, int n_sm, cudaStream_t st
         lb_multi_kernel<D, 1, QT><<<grid, LB_THREADS, smem, st>>>(a);
 }
 
+// Shared memory of the windowed kernel: two buffers of lo and hi windows.
+constexpr size_t lb_win_bytes(int qt, int ch, int win) { return (size_t)16 * qt * ch * win; }
+
+template <int D, int QT>
+static void lb_win_launch(const LbArgs &a, int form, cudaStream_t st)
+{
+    constexpr int CH = chunk_floats(D);
+    const int nch_env = a.env_floats / CH;
+    LbArgs w = a;
+    if (w.win_chunks <= 0) {
+        // about 96 KB of windows: two CTAs per SM
+        int win = (int)((96 * 1024) / lb_win_bytes(QT, CH, 1));
+        w.win_chunks = win < nch_env ? win : nch_env;
+    }
+    if (lb_win_bytes(QT, CH, w.win_chunks) > 192 * 1024)
+        w.win_chunks = (int)((192 * 1024) / lb_win_bytes(QT, CH, 1));
+    if (w.win_chunks < 1)
+        w.win_chunks = 1;
+    const size_t smem = lb_win_bytes(QT, CH, w.win_chunks);
+    const int nser = a.c_end - a.c_begin;
+    dim3 grid((nser + LB_THREADS - 1) / LB_THREADS, (a.nq + QT - 1) / QT);
+    if (form == 0)
+        lb_win_kernel<D, 0, QT><<<grid, LB_THREADS, smem, st>>>(w);
+    else
+        lb_win_kernel<D, 1, QT><<<grid, LB_THREADS, smem, st>>>(w);
+}
+
 template <int D>
 static void lb_launch_d(const LbArgs &a, int form, int n_sm, cudaStream_t st)
 {
-    // several queries: the multi-query kernel with the largest tile whose
-    // envelopes fit in shared memory
+    // several queries: the multi-query kernel with the requested tile (16
+    // unless set), whole envelopes when they fit in shared memory, else
+    // windows of them
     const size_t per_q = (size_t)a.env_floats * 4 * 2;
     if (a.nq >= 4 && !a.single_query_kernel) {
         const int want = a.qtile > 0 ? a.qtile : 16;
-        if (want >= 16 && a.nq >= 16 && 16 * per_q <= 192 * 1024)
-            return lb_multi_launch<D, 16>(a, form, n_sm, st);
-        if (want >= 8 && a.nq >= 8 && 8 * per_q <= 192 * 1024)
-            return lb_multi_launch<D, 8>(a, form, n_sm, st);
-        if (4 * per_q <= 192 * 1024)
-            return lb_multi_launch<D, 4>(a, form, n_sm, st);
+        const int qt = (want >= 16 && a.nq >= 16) ? 16 : (want >= 8 && a.nq >= 8) ? 8 : 4;
+        const bool whole = a.win_chunks <= 0 && qt * per_q <= 192 * 1024;
+        if (qt == 16)
+            return whole ? lb_multi_launch<D, 16>(a, form, n_sm, st) : lb_win_launch<D, 16>(a, form, st);
+        if (qt == 8)
+            return whole ? lb_multi_launch<D, 8>(a, form, n_sm, st) : lb_win_launch<D, 8>(a, form, st);
+        return whole ? lb_multi_launch<D, 4>(a, form, n_sm, st) : lb_win_launch<D, 4>(a, form, st);
     }
     const size_t smem = (size_t)a.env_floats * 4 * 2;
     auto kern = form == 0 ? lb_kernel<D, 0> : lb_kernel<D, 1>;

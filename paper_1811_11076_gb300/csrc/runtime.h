@@ -115,7 +115,8 @@ struct knn_db {
     cudaStream_t cap_stream = nullptr;    // private stream used only to capture graphs
     std::map<std::tuple<int, int, int>, knn::DpChoice> tuned;  // (kind, r, n) -> config
     bool tuning = false;                  // autotuner running: one DP segment per bucket
-    int lb_qtile[2] = {0, 0};             // queries per LB pass per distance (0: largest)
+    int lb_qtile[2] = {0, 0};             // queries per LB pass per distance (0: 16)
+    int lb_window[2] = {0, 0};            // LB envelope window in chunks (0: automatic)
     std::vector<double> seg_ms;           // profile: DP time per segment of the last scan
     std::vector<int> seg_first_bucket;    // first bucket of each segment of the last scan
     ~knn_db()

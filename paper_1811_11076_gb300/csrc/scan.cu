@@ -380,6 +380,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         l.thr = ws.thr.as<float>();
         l.mu_prune = pl.mg.mu_prune;
         l.qtile = db->lb_qtile[kind];
+        l.win_chunks = db->lb_window[kind];
         if (store) {
             l.out_lb = ws.lb_all.as<float>();
             l.out_lb_stride = db->N;

@@ -350,6 +350,36 @@ def test_every_dp_shape_gives_identical_results(kw, kind):
     db.close()
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d,lengths,nq", [(3, (40, 300), 21), (16, (300, 700), 9)])
+def test_lb_tiles_and_windows_give_identical_results(kw, kind, d, lengths, nq):
+    """LB_Box with 4, 8 or 16 queries per pass, whole envelopes or windows of
+    them (several sizes, ragged last window, a partial query tile): every
+    variant bounds the same way, so every scan returns the oracle's result."""
+    w = make_workload(n_series=700 if d == 3 else 300, n_queries=nq, d=d, length_range=lengths,
+                      n_classes=6, seed=31 + d)
+    band, k = 0.1, 4
+    oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(band), kind=kind, k=k)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    assert db.get_lb_tile(kind) == (0, 0)
+    ref = None
+    for qt in (4, 8, 16):
+        for win in (0, 1, 5, 64):
+            db.set_lb_tile(kind, qt, win)
+            assert db.get_lb_tile(kind) == (qt, win)
+            for seed in (kw.SEED_GREEDY, kw.SEED_LB, kw.SEED_NONE):
+                ids, dist = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind, seed=seed)
+                ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+                check_knn(ids, dist, oids, odist, kind, k)
+                if ref is None:
+                    ref = (ids, dist)
+                assert (ids == ref[0]).all() and (dist == ref[1]).all()
+    for bad in ((kind, 5, 0), (kind, 16, -1), (2, 16, 0)):
+        with pytest.raises(kw.KnnError):
+            db.set_lb_tile(*bad)
+    db.close()
+
+
 def test_autotune_and_cache(kw, tmp_path):
     w = make_workload(n_series=3000, n_queries=16, d=3, length_range=(60, 200), n_classes=8,
                       seed=16)
