@@ -144,6 +144,7 @@ def workload(world: int):
     from synthdata import WORKLOADS, make_workload
     kw = dict(WORKLOADS[WORKLOAD])
     kw["n_queries"] = N_QUERIES * world
+    kw["n_series"] = N_SERIES
     return make_workload(**kw)
 
 
@@ -473,6 +474,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=list(BENCH))
     ap.add_argument("--queries", type=int, default=0,
                     help="queries per GPU (default: the workload's; smaller only for profiling)")
+    ap.add_argument("--series", type=int, default=0,
+                    help="database series (default: the workload's; smaller only for profiling)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
@@ -481,6 +484,8 @@ def main():
     select_workload(args.workload)
     if args.queries:
         globals()["N_QUERIES"] = args.queries
+    if args.series:
+        globals()["N_SERIES"] = args.series
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

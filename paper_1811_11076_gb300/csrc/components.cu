@@ -185,6 +185,8 @@ static knn_status bound_common(knn_db *db, const float *query, int64_t m, float 
             l.out_lb_stride = db->N;
             l.stats = ctrl->stats;
             l.status = &ctrl->status;
+            l.n_lo = b.n_lo;
+            l.n_hi = b.n_hi;
             launch_lb(l, db->deff, form, db->n_sm, st);
         }
     }

@@ -96,7 +96,11 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
     bool active = false, done = false;
     int s0 = 0;
 
-    int wbase = 0, wcur = 32;
+    // queue items are taken one per group of the warp per atomic: a pair
+    // can run for a long time (long series, high d), so larger grabs would
+    // leave a long tail of warps working through their private surplus
+    const int grab = 32 / G;
+    int wbase = 0, wcur = grab;
     const int n_items = (int)min((int64_t)*a.n_items, a.items_cap);
 
     unsigned long long st_calls = 0, st_aband = 0, st_cells = 0, st_pruned = 0;
@@ -108,14 +112,14 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
             const unsigned needy = __ballot_sync(KNN_FULL_MASK, need && lam == 0);
             if (needy == 0)
                 break;
-            if (wcur >= 32) {
+            if (wcur >= grab) {
                 int b = 0;
                 if (lane == 0)
-                    b = atomicAdd(a.head, 32);
+                    b = atomicAdd(a.head, grab);
                 wbase = __shfl_sync(KNN_FULL_MASK, b, 0);
                 wcur = 0;
             }
-            const int avail = 32 - wcur;
+            const int avail = grab - wcur;
             const int rank = __popc(needy & lt_mask);
             const int served = min(__popc(needy), avail);
             if (need && rank < avail) {

@@ -8,8 +8,8 @@
 // (Section 2.1 recurrences, no pruning) before the cut is taken.  Candidates
 // outside the band are ordered correctly by their FP32 values already.
 //
-// Three launches: mark (sort, pick entries to re-score), rescore (one thread
-// per picked entry, band rows in global scratch), output (final order, cut).
+// Three launches: mark (sort, pick entries to re-score), rescore (one CTA per
+// picked entry, band rows in shared memory), output (final order, cut).
 #include "common.cuh"
 #include "internal.h"
 
@@ -17,33 +17,36 @@ namespace knn {
 
 constexpr int FIN_THREADS = 128;
 
-// Banded DP in FP64 for one pair, computed by one warp along anti-diagonals
-// t = i + j: every cell of an anti-diagonal is independent, lanes take the
-// band diagonals delta = j - i of the right parity in strides of 64, and the
-// two previous anti-diagonals live in shared memory (indexed by delta + r + 1,
-// with an infinite sentinel on both sides).  kind 0: DTW (sum of squared
-// costs); kind 1: DK^2 (max of squared costs).  Each cell applies exactly the
-// operations of the recurrence (products and sums rounded separately, no
-// fused multiply-add, coordinates in order), so the value equals that of a
-// sequential double-precision evaluation regardless of the sweep order.
-// Shared memory: 3 * (2r + 3) doubles.  Returns the value in lane 0 and all
-// lanes.
-__device__ double dp_fp64_warp(const float *s, int m, const float *t, int n, int d, int r,
-                               int kind, double *buf)
+// Banded DP in FP64 for one pair, computed by the threads of one CTA along
+// anti-diagonals t = i + j: every cell of an anti-diagonal is independent,
+// threads take the band diagonals delta = j - i of the right parity in
+// strides of 2 * blockDim.x, and the two previous anti-diagonals live in
+// shared memory (indexed by delta + r + 1, with an infinite sentinel on both
+// sides).  Every in-band slot is rewritten on each anti-diagonal of its
+// parity (with +inf outside the matrix) and slots of the other parity are
+// never read, so the three rows rotate without clearing.  kind 0: DTW (sum
+// of squared costs); kind 1: DK^2 (max of squared costs).  Each cell applies
+// exactly the operations of the recurrence (products and sums rounded
+// separately, no fused multiply-add, coordinates in order), so the value
+// equals that of a sequential double-precision evaluation regardless of the
+// sweep order.  Shared memory: 3 * (2r + 3) doubles.  Called by all threads
+// of the CTA; returns the value in every thread.
+__device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int d, int r,
+                              int kind, double *buf)
 {
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, nt = blockDim.x;
     if (abs(m - n) > r)
         return (double)KNN_INF;
     const int W = 2 * r + 3;
     double *A = buf, *B = buf + W, *Cc = buf + 2 * W;  // t-2, t-1, t
-    for (int b = lane; b < 3 * W; b += 32)
+    for (int b = tid; b < 3 * W; b += nt)
         buf[b] = (double)KNN_INF;
-    __syncwarp();
+    __syncthreads();
     const int tmax = m + n - 2;
     for (int tt = 0; tt <= tmax; ++tt) {
         // diagonals delta in [-r, r] with delta = tt (mod 2)
         const int d0 = -r + (((tt + r) & 1) ? 1 : 0);
-        for (int dl = d0 + 2 * lane; dl <= r; dl += 64) {
+        for (int dl = d0 + 2 * tid; dl <= r; dl += 2 * nt) {
             const int i2 = tt - dl, j2 = tt + dl;  // 2i, 2j
             const int i = i2 >> 1, j = j2 >> 1;
             double v = (double)KNN_INF;
@@ -64,18 +67,24 @@ __device__ double dp_fp64_warp(const float *s, int m, const float *t, int n, int
             }
             Cc[dl + r + 1] = v;
         }
-        __syncwarp();
-        // rotate: the new t-2 is the old t-1; reset the outgoing row to +inf
+        __syncthreads();
+        // rotate: the new t-2 is the old t-1
         double *old = A;
         A = B;
         B = Cc;
         Cc = old;
-        for (int b = lane; b < W; b += 32)
-            Cc[b] = (double)KNN_INF;
-        __syncwarp();
     }
     // the end cell (m-1, n-1) lies on anti-diagonal tmax, now in B
     return B[(n - m) + r + 1];
+}
+
+// Threads of the re-scoring CTA for band rows of `row` slots: about one
+// diagonal of each parity per thread.
+static int fp64_threads(int row)
+{
+    const int half = (row + 1) / 2;
+    int t = (half + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > 256 ? 256 : t);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,9 +191,9 @@ __global__ void __launch_bounds__(FIN_THREADS) fin_mark_kernel(const FinArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// 2. rescore: one warp (one block) per picked entry
+// 2. rescore: one CTA per picked entry
 
-__global__ void __launch_bounds__(32) fin_rescore_kernel(const FinArgs a)
+__global__ void __launch_bounds__(256) fin_rescore_kernel(const FinArgs a)
 {
     extern __shared__ double rbuf[];
     const int n_rer = min(*a.rer_count, a.rer_cap);
@@ -202,11 +211,11 @@ __global__ void __launch_bounds__(32) fin_rescore_kernel(const FinArgs a)
                 atomicOr(a.status, KNN_DEV_BAD_SHAPE);
             continue;
         }
-        const double v = dp_fp64_warp(a.q + a.q_off[qb], m, a.db + a.db_off_by_id[id], n, a.d, r,
-                                      a.kind, rbuf);
+        const double v = dp_fp64_cta(a.q + a.q_off[qb], m, a.db + a.db_off_by_id[id], n, a.d, r,
+                                     a.kind, rbuf);
         if (threadIdx.x == 0)
             a.fin_vals[(size_t)qb * a.fin_width + i] = v;
-        __syncwarp();
+        __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats)
         atomicAdd(a.stats + STAT_RERANKED, (unsigned long long)n_rer);
@@ -302,12 +311,13 @@ void launch_finalize(const FinArgs &a, cudaStream_t st)
     const size_t smem_out = (size_t)a.sort_cap * (sizeof(unsigned long long) + sizeof(double));
     fin_mark_kernel<<<a.nq, FIN_THREADS, smem_mark, st>>>(a);
     const size_t smem_rer = (size_t)3 * (a.rer_row + 2) * sizeof(double);
-    fin_rescore_kernel<<<a.rer_cap < 4096 ? a.rer_cap : 4096, 32, smem_rer, st>>>(a);
+    fin_rescore_kernel<<<a.rer_cap < 4096 ? a.rer_cap : 4096, fp64_threads(a.rer_row), smem_rer,
+                         st>>>(a);
     fin_out_kernel<<<a.nq, FIN_THREADS, smem_out, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------
-// FP64 pair program: one warp (one block) per pair
+// FP64 pair program: one 32-thread CTA per pair (many pairs run at once)
 
 __global__ void __launch_bounds__(32) pairwise64_kernel(const float *a, const int64_t *a_off,
                                                         const float *b, const int64_t *b_off,
@@ -323,10 +333,10 @@ __global__ void __launch_bounds__(32) pairwise64_kernel(const float *a, const in
         const int r = band_radius(m, nn, band);
         double v = -1.0;
         if (2 * r + 1 <= row)
-            v = dp_fp64_warp(a + a_off[ia] * d, m, b + b_off[ib] * d, nn, d, r, kind, pbuf);
+            v = dp_fp64_cta(a + a_off[ia] * d, m, b + b_off[ib] * d, nn, d, r, kind, pbuf);
         if (threadIdx.x == 0)
             out[p] = v < 0.0 ? v : (kind == 0 ? v : sqrt(v));
-        __syncwarp();
+        __syncthreads();
     }
 }
 

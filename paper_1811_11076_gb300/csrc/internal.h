@@ -63,6 +63,9 @@ struct LbArgs {
     int qtile;                 // queries per CTA of the multi-query kernel (0: 16)
     int win_chunks;            // > 0: windowed multi-query kernel with windows of this many
                                // chunks; 0: whole envelopes when they fit, else windowed
+    const int *q_order;        // multi-query kernels: batch queries in tile order (queries
+                               // sorted by length; nullable = batch order)
+    int n_lo, n_hi;            // shortest / longest series of the bucket
 };
 void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();

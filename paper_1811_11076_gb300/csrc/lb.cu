@@ -364,7 +364,7 @@ __device__ __forceinline__ void lb_multi_chunk(const float4 *__restrict__ x4c, c
 }
 
 template <int QT>
-__device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float (&lim)[QT])
+__device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float *lim)
 {
     bool all_over = true;
 #pragma unroll
@@ -373,19 +373,68 @@ __device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float 
     return all_over;
 }
 
-// Per-thread set-up shared by the multi-query kernels: query lengths and the
-// pruning limits of the tile (filter mode; -1 for missing queries so that
-// they never hold a series back).
+// Query of slot j of the tile starting at q0 (tiles follow the length order).
+__device__ __forceinline__ int lb_qslot(const LbArgs &a, int q0, int j)
+{
+    return a.q_order ? a.q_order[q0 + j] : q0 + j;
+}
+
+// Set-up shared by the multi-query kernels, into shared memory: query
+// lengths and the pruning limits of the tile (filter mode; -1 for missing
+// queries so that they never hold a series back).  Ends with a barrier.
 template <int QT>
-__device__ __forceinline__ void lb_multi_setup(const LbArgs &a, int q0, int nqt, int (&mq)[QT],
-                                               float (&lim)[QT])
+__device__ __forceinline__ void lb_multi_setup(const LbArgs &a, int q0, int nqt, int *mq, float *lim)
+{
+    const int j = threadIdx.x;
+    if (j < QT) {
+        const int qb = j < nqt ? lb_qslot(a, q0, j) : 0;
+        mq[j] = j < nqt ? a.q_len[qb] : 1;
+        lim[j] = j >= nqt ? -1.f : a.items ? ld_volatile_f32(a.thr + qb) * a.mu_prune : KNN_INF;
+    }
+    __syncthreads();
+}
+
+// Bounds of a new series start at 0, or at +inf for a query whose band
+// cannot reach the end cell (|m - n| > r): such a pair is never a candidate,
+// and an infinite bound lets the series be abandoned as soon as the feasible
+// queries are done with it.
+template <int QT>
+__device__ __forceinline__ void lb_multi_init(const LbArgs &a, const int *mq, int n,
+                                              float (&acc)[QT])
 {
 #pragma unroll
-    for (int j = 0; j < QT; ++j) {
-        mq[j] = j < nqt ? a.q_len[q0 + j] : 1;
-        lim[j] = (a.items && j < nqt) ? ld_volatile_f32(a.thr + q0 + j) * a.mu_prune : KNN_INF;
-        if (j >= nqt)
-            lim[j] = -1.f;
+    for (int j = 0; j < QT; ++j)
+        acc[j] = abs(mq[j] - n) <= band_radius(mq[j], n, a.band) ? 0.f : KNN_INF;
+}
+
+// True if some query of the tile can reach the end cell of some series
+// length of the bucket; a CTA whose tile has none skips the bucket.
+template <int QT>
+__device__ __forceinline__ bool lb_tile_feasible(const LbArgs &a, const int *mq, int nqt)
+{
+    bool any = false;
+    for (int n = a.n_lo + (int)threadIdx.x; n <= a.n_hi && !any; n += blockDim.x)
+#pragma unroll
+        for (int j = 0; j < QT; ++j)
+            any |= j < nqt && abs(mq[j] - n) <= band_radius(mq[j], n, a.band);
+    return __syncthreads_or(any) != 0;
+}
+
+// The CTA's series against a tile with no feasible pair: bounds +inf
+// (store mode), counted as band-infeasible.
+template <int QT>
+__device__ __forceinline__ void lb_tile_skip(const LbArgs &a, int q0, int nqt, int i0, int stride,
+                                             unsigned long long &st_pairs,
+                                             unsigned long long &st_inf)
+{
+    const int nser = a.c_end - a.c_begin;
+    for (int i = i0; i < nser; i += stride) {
+        const int c = a.c_begin + i;
+        if (a.out_lb)
+            for (int j = 0; j < nqt; ++j)
+                a.out_lb[(int64_t)lb_qslot(a, q0, j) * a.out_lb_stride + c] = KNN_INF;
+        st_pairs += nqt;
+        st_inf += nqt;
     }
 }
 
@@ -393,7 +442,7 @@ __device__ __forceinline__ void lb_multi_setup(const LbArgs &a, int q0, int nqt,
 // survivor queue (filter mode), and the counters.  Warp-converged.
 template <int QT>
 __device__ __forceinline__ void lb_multi_finish(const LbArgs &a, int q0, int nqt,
-                                                const int (&mq)[QT], const float (&lim)[QT],
+                                                const int *mq, const float *lim,
                                                 const float (&acc)[QT], bool valid, int c, int n,
                                                 int lane, unsigned long long &st_pairs,
                                                 unsigned long long &st_inf,
@@ -403,7 +452,7 @@ __device__ __forceinline__ void lb_multi_finish(const LbArgs &a, int q0, int nqt
     for (int j = 0; j < QT; ++j) {
         if (j >= nqt)
             break;
-        const int qb = q0 + j;
+        const int qb = lb_qslot(a, q0, j);
         const int r = band_radius(mq[j], n, a.band);
         const bool feasible = valid && abs(mq[j] - n) <= r;
         const float lb = feasible ? acc[j] : KNN_INF;
@@ -477,6 +526,18 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
     const int st4 = a.env_floats / 4;
     const float4 *lo_s = env_s;
     const float4 *hi_s = env_s + QT * st4;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
+
+    // filter mode: a series is done once every bound exceeds its limit
+    __shared__ int mq[QT];
+    __shared__ float lim[QT];
+    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
+    if (!lb_tile_feasible<QT>(a, mq, nqt)) {
+        lb_tile_skip<QT>(a, q0, nqt, blockIdx.x * LB_THREADS + threadIdx.x, gridDim.x * LB_THREADS,
+                         st_pairs, st_inf);
+        lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
+        return;
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -487,9 +548,9 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
         const uint32_t bytes = (uint32_t)a.env_floats * 4u;
         mbar_expect_tx(&bar, 2u * bytes * (uint32_t)nqt);
         for (int j = 0; j < nqt; ++j) {
-            tma_bulk_g2s(env_s + j * st4, a.env_lo + (int64_t)(q0 + j) * a.env_stride, bytes, &bar);
-            tma_bulk_g2s(env_s + (QT + j) * st4, a.env_hi + (int64_t)(q0 + j) * a.env_stride, bytes,
-                         &bar);
+            const int64_t src = (int64_t)lb_qslot(a, q0, j) * a.env_stride;
+            tma_bulk_g2s(env_s + j * st4, a.env_lo + src, bytes, &bar);
+            tma_bulk_g2s(env_s + (QT + j) * st4, a.env_hi + src, bytes, &bar);
         }
     }
     if (!mbar_wait0(&bar)) {
@@ -498,10 +559,6 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
         return;
     }
 
-    int mq[QT];
-    float lim[QT];  // filter mode: a series is done once every bound exceeds its limit
-    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
-    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
     const int nser = a.c_end - a.c_begin;
     const int span = (nser + LB_THREADS - 1) / LB_THREADS * LB_THREADS;
     for (int i = blockIdx.x * LB_THREADS + threadIdx.x; i < span; i += gridDim.x * LB_THREADS) {
@@ -509,9 +566,7 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
         const int c = a.c_begin + (valid ? i : 0);
         const int n = valid ? a.db_len[c] : 0;
         float acc[QT];
-#pragma unroll
-        for (int j = 0; j < QT; ++j)
-            acc[j] = 0.f;
+        lb_multi_init<QT>(a, mq, n, acc);
         const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
         const int nch = (n + PPC - 1) / PPC;
         for (int ch = 0; ch < nch; ++ch) {
@@ -574,6 +629,17 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
     const int lane = threadIdx.x & 31;
     const int nch_env = a.env_floats / CH;
     const int W = (nch_env + WCH - 1) / WCH;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
+
+    __shared__ int mq[QT];
+    __shared__ float lim[QT];
+    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
+    if (!lb_tile_feasible<QT>(a, mq, nqt)) {
+        lb_tile_skip<QT>(a, q0, nqt, blockIdx.x * LB_THREADS + threadIdx.x, 1 << 30, st_pairs,
+                         st_inf);
+        lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
+        return;
+    }
 
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -589,7 +655,7 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
         float4 *dst = env_s + (w & 1) * buf4;
         mbar_expect_tx(&bar[w & 1], 2u * bytes * (uint32_t)nqt);
         for (int j = 0; j < nqt; ++j) {
-            const int64_t src = (int64_t)(q0 + j) * a.env_stride + (int64_t)c0 * CH;
+            const int64_t src = (int64_t)lb_qslot(a, q0, j) * a.env_stride + (int64_t)c0 * CH;
             tma_bulk_g2s(dst + j * wst4, a.env_lo + src, bytes, &bar[w & 1]);
             tma_bulk_g2s(dst + (QT + j) * wst4, a.env_hi + src, bytes, &bar[w & 1]);
         }
@@ -600,9 +666,6 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
             issue(1);
     }
 
-    int mq[QT];
-    float lim[QT];
-    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
     const int nser = a.c_end - a.c_begin;
     const int i = blockIdx.x * LB_THREADS + threadIdx.x;
     const bool valid = i < nser;
@@ -611,10 +674,7 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
     const int nch = (n + PPC - 1) / PPC;
     const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
     float acc[QT];
-#pragma unroll
-    for (int j = 0; j < QT; ++j)
-        acc[j] = 0.f;
-    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
+    lb_multi_init<QT>(a, mq, n, acc);
 
     int w = 0;
     bool failed = false;

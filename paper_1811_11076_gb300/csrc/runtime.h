@@ -45,6 +45,7 @@ struct Bucket {
 struct Workspace {
     DevBuf q_raw, q_src_off;            // staged caller queries (host input)
     DevBuf qbuf, q_off, q_len;          // repacked queries of the batch
+    DevBuf q_order;                     // batch queries sorted by length (LB tiles)
     DevBuf env_lo, env_hi;
     DevBuf thr, slots, ub_slots;
     DevBuf items, item_lb;

@@ -25,6 +25,7 @@ struct Segment {
 struct Plan {
     int nq = 0;
     std::vector<int> m;
+    std::vector<int> order;     // batch queries by length (stable): LB_Box query tiles
     std::vector<int64_t> qoff;  // float offsets of the repacked queries
     int64_t qfloats = 0;
     int max_m = 0;
@@ -89,6 +90,13 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
         pl.qfloats += (int64_t)((m + PPC - 1) / PPC) * CH;
         pl.max_m = std::max(pl.max_m, m);
     }
+    // LB_Box tiles of queries with similar lengths share the buckets their
+    // bands can reach; a tile reaching none of a bucket skips it
+    pl.order.resize(nq);
+    for (int i = 0; i < nq; ++i)
+        pl.order[i] = i;
+    std::stable_sort(pl.order.begin(), pl.order.end(),
+                     [&](int x, int y) { return pl.m[x] < pl.m[y]; });
     pl.env_stride = 0;
     for (auto &b : db->buckets)
         pl.env_stride = std::max<int64_t>(pl.env_stride, (int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
@@ -174,6 +182,7 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(qbuf, sizeof(float) * pl.qfloats);
     G_(q_off, sizeof(int64_t) * nq);
     G_(q_len, sizeof(int) * nq);
+    G_(q_order, sizeof(int) * nq);
     G_(env_lo, sizeof(float) * nq * pl.env_stride);
     G_(env_hi, sizeof(float) * nq * pl.env_stride);
     G_(thr, sizeof(float) * nq);
@@ -381,6 +390,9 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         l.mu_prune = pl.mg.mu_prune;
         l.qtile = db->lb_qtile[kind];
         l.win_chunks = db->lb_window[kind];
+        l.q_order = ws.q_order.as<int>();
+        l.n_lo = b.n_lo;
+        l.n_hi = b.n_hi;
         if (store) {
             l.out_lb = ws.lb_all.as<float>();
             l.out_lb_stride = db->N;
@@ -665,6 +677,9 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ws.q_len.p, pl.m.data(), sizeof(int) * nq, cudaMemcpyHostToDevice,
                                 st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ws.q_order.p, pl.order.data(), sizeof(int) * nq,
+                                cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(st);  // host vectors go out of scope
         if (e != cudaSuccess)
