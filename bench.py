@@ -258,6 +258,8 @@ def run_gpu(args):
     r = int(np.float64(np.float32(BAND)) * LENGTH)
     graph = BENCH[WORKLOAD]["graph"] and not args.no_graph
     for kind in kinds:
+        if args.lb_compaction:
+            dbs[kind].set_lb_tile(kind, 0, 0, args.lb_compaction)
         if args.shape:
             P, G = (int(v) for v in args.shape.split(","))
             dbs[kind].set_dp_shape(kind, r, LENGTH, P, G)
@@ -480,6 +482,8 @@ def main():
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default="", help="P,G: fix the DP shape instead of tuning it")
+    ap.add_argument("--lb-compaction", type=int, default=0, choices=[0, 1, 2],
+                    help="LB_Box compaction: 0 automatic, 1 never, 2 always")
     args = ap.parse_args()
     select_workload(args.workload)
     if args.queries:

@@ -209,13 +209,16 @@ KNN_API int32_t knn_dp_shapes(int32_t d, int32_t *P_list, int32_t cap);
  * window_chunks = 0: a CTA stages the tile's whole envelopes in shared
  * memory when they fit (2 * 4 * qtile * padded length * d bytes <= 192 KB)
  * and windows of them otherwise; > 0: always windows of that many chunks of
- * lcm(d', 4) floats (clamped to what fits).  The result of a scan does not
- * depend on either value.  KNN_ERR_INVALID for other qtile values or a
- * negative window. */
+ * lcm(d', 4) floats (clamped to what fits).  compaction (filter mode with
+ * whole envelopes; the early abandoning of Section 4 applied to the bound):
+ * 0 = when a CTA walks at least 4 batches of series of at least 16 chunks,
+ * 1 = never, 2 = whenever the series have at least 8 chunks.  The result of a
+ * scan depends on none of these values.  KNN_ERR_INVALID for other qtile or
+ * compaction values or a negative window. */
 KNN_API knn_status knn_set_lb_tile(knn_db *db, int32_t distance, int32_t qtile,
-                                   int32_t window_chunks);
+                                   int32_t window_chunks, int32_t compaction);
 KNN_API knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qtile,
-                                   int32_t *window_chunks);
+                                   int32_t *window_chunks, int32_t *compaction);
 
 /* ---------------------------------------------------------------------- */
 /* Components (each is one step of the scan, exposed for verification and  */

@@ -112,8 +112,8 @@ def lib() -> C.CDLL:
     L.knn_set_dp_shape.argtypes = [vp] + [C.c_int32] * 5
     L.knn_get_dp_shape.argtypes = [vp] + [C.c_int32] * 3 + [C.POINTER(C.c_int32)] * 2
     L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
-    L.knn_set_lb_tile.argtypes = [vp] + [C.c_int32] * 3
-    L.knn_get_lb_tile.argtypes = [vp, C.c_int32] + [C.POINTER(C.c_int32)] * 2
+    L.knn_set_lb_tile.argtypes = [vp] + [C.c_int32] * 4
+    L.knn_get_lb_tile.argtypes = [vp, C.c_int32] + [C.POINTER(C.c_int32)] * 3
     L.knn_pairwise_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp, C.c_int64,
                                        C.c_int32, C.c_float, C.c_int32, C.c_int32, vp, vp]
     L.knn_encoder_num_params.restype = C.c_int32
@@ -265,14 +265,15 @@ class KnnDB:
     def set_dp_shape(self, distance: int, r: int, n: int, P: int, G: int):
         _check(lib().knn_set_dp_shape(self._h, distance, r, n, P, G))
 
-    def set_lb_tile(self, distance: int, qtile: int = 0, window_chunks: int = 0):
-        """Queries per LB_Box pass and the envelope window (0: automatic)."""
-        _check(lib().knn_set_lb_tile(self._h, distance, qtile, window_chunks))
+    def set_lb_tile(self, distance: int, qtile: int = 0, window_chunks: int = 0,
+                    compaction: int = 0):
+        """Queries per LB_Box pass, envelope window and compaction (0: automatic)."""
+        _check(lib().knn_set_lb_tile(self._h, distance, qtile, window_chunks, compaction))
 
     def get_lb_tile(self, distance: int):
-        q, w = C.c_int32(), C.c_int32()
-        _check(lib().knn_get_lb_tile(self._h, distance, C.byref(q), C.byref(w)))
-        return q.value, w.value
+        q, w, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().knn_get_lb_tile(self._h, distance, C.byref(q), C.byref(w), C.byref(c)))
+        return q.value, w.value, c.value
 
     def get_dp_shape(self, distance: int, r: int, n: int):
         P, G = C.c_int32(), C.c_int32()

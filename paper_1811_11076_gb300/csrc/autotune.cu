@@ -274,7 +274,7 @@ extern "C" knn_status knn_get_dp_shape(knn_db *db, int32_t distance, int32_t r, 
 }
 
 extern "C" knn_status knn_set_lb_tile(knn_db *db, int32_t distance, int32_t qtile,
-                                      int32_t window_chunks)
+                                      int32_t window_chunks, int32_t compaction)
 {
     if (!db)
         return set_error(KNN_ERR_INVALID, "db is NULL");
@@ -284,20 +284,24 @@ extern "C" knn_status knn_set_lb_tile(knn_db *db, int32_t distance, int32_t qtil
         return set_error(KNN_ERR_INVALID, "qtile must be 0, 4, 8 or 16");
     if (window_chunks < 0)
         return set_error(KNN_ERR_INVALID, "window_chunks must be >= 0");
+    if (compaction < 0 || compaction > 2)
+        return set_error(KNN_ERR_INVALID, "compaction must be 0, 1 or 2");
     db->lb_qtile[distance] = qtile;
     db->lb_window[distance] = window_chunks;
+    db->lb_compact[distance] = compaction;
     return KNN_OK;
 }
 
 extern "C" knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qtile,
-                                      int32_t *window_chunks)
+                                      int32_t *window_chunks, int32_t *compaction)
 {
-    if (!db || !qtile || !window_chunks)
+    if (!db || !qtile || !window_chunks || !compaction)
         return set_error(KNN_ERR_INVALID, "NULL argument");
     if (distance != KNN_DTW && distance != KNN_DK)
         return set_error(KNN_ERR_INVALID, "distance must be KNN_DTW or KNN_DK");
     *qtile = db->lb_qtile[distance];
     *window_chunks = db->lb_window[distance];
+    *compaction = db->lb_compact[distance];
     return KNN_OK;
 }
 

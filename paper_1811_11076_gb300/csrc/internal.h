@@ -66,7 +66,13 @@ struct LbArgs {
     const int *q_order;        // multi-query kernels: batch queries in tile order (queries
                                // sorted by length; nullable = batch order)
     int n_lo, n_hi;            // shortest / longest series of the bucket
+    float *lbq;                // filter mode: per-CTA survivor queues of the compacting
+                               // kernel (nullable: no compaction)
+    int compact;               // 0 automatic, 1 never, 2 whenever possible
+    int k1, k2;                // compaction checkpoints in chunks (set by the launcher)
 };
+// Floats of survivor-queue scratch one LB launch may need for nq queries.
+size_t lb_queue_floats(int n_sm, int nq);
 void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();
 

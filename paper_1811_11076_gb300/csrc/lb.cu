@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
         tma_bulk_g2s(env_s + a.env_floats / 4, a.env_hi + (int64_t)qb * a.env_stride, bytes, &bar);
     }
     if (!mbar_wait0(&bar)) {
+        mbar_wait0(&bar);  // once more (bounded) for the copies still in flight
         if (lane == 0)
             atomicOr(a.status, KNN_DEV_TIMEOUT);
         return;
@@ -554,6 +555,7 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
         }
     }
     if (!mbar_wait0(&bar)) {
+        mbar_wait0(&bar);  // once more (bounded) for the copies still in flight
         if (lane == 0)
             atomicOr(a.status, KNN_DEV_TIMEOUT);
         return;
@@ -583,6 +585,171 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
                             st_pruned);
     }
     lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
+}
+
+// Whole envelopes with compaction of the early abandoning (filter mode).  In
+// a 256-series batch every thread walks its series in lockstep with the
+// others, so the batch runs as long as its slowest series even when most are
+// already past every limit.  Here a batch runs to a first checkpoint K1; the
+// series still alive for some query (index and QT partial bounds) go to a
+// per-CTA queue in global scratch, and whenever 256 of them are waiting they
+// run together to K2, the survivors of that to a second queue and on to the
+// end.  Every group of 256 starts at the same chunk, so envelope reads stay
+// broadcasts.  Bounds and decisions are those of lb_multi_kernel.
+constexpr int LBQ_CAP = 512;  // entries per queue: < 256 waiting + 256 arriving
+
+template <int D, int FORM, int QT>
+__global__ void __launch_bounds__(LB_THREADS, 2) lb_compact_kernel(const LbArgs a)
+{
+    constexpr int CH = chunk_floats(D);
+    constexpr int PPC = chunk_points(D);
+    constexpr int F4 = CH / 4;
+    extern __shared__ __align__(128) float4 env_s[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int qcnt[2], qhead[2], qpush[2];
+
+    const int q0 = blockIdx.y * QT;
+    const int nqt = min(QT, a.nq - q0);
+    const int lane = threadIdx.x & 31;
+    const int st4 = a.env_floats / 4;
+    const float4 *lo_s = env_s;
+    const float4 *hi_s = env_s + QT * st4;
+    unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_points = 0;
+
+    __shared__ int mq[QT];
+    __shared__ float lim[QT];
+    lb_multi_setup<QT>(a, q0, nqt, mq, lim);
+    if (!lb_tile_feasible<QT>(a, mq, nqt)) {
+        lb_tile_skip<QT>(a, q0, nqt, blockIdx.x * LB_THREADS + threadIdx.x, gridDim.x * LB_THREADS,
+                         st_pairs, st_inf);
+        lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 2) {
+        qcnt[threadIdx.x] = 0;
+        qhead[threadIdx.x] = 0;
+        qpush[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)a.env_floats * 4u;
+        mbar_expect_tx(&bar, 2u * bytes * (uint32_t)nqt);
+        for (int j = 0; j < nqt; ++j) {
+            const int64_t src = (int64_t)lb_qslot(a, q0, j) * a.env_stride;
+            tma_bulk_g2s(env_s + j * st4, a.env_lo + src, bytes, &bar);
+            tma_bulk_g2s(env_s + (QT + j) * st4, a.env_hi + src, bytes, &bar);
+        }
+    }
+    if (!mbar_wait0(&bar)) {
+        mbar_wait0(&bar);  // once more (bounded) for the copies still in flight
+        if (lane == 0)
+            atomicOr(a.status, KNN_DEV_TIMEOUT);
+        return;
+    }
+
+    // queue q of this CTA: [CAP] series indices (as float bits), then QT rows
+    // of [CAP] partial bounds
+    float *qmem = a.lbq + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * 2 * LBQ_CAP * (QT + 1);
+    const int nser = a.c_end - a.c_begin;
+    int next = blockIdx.x * LB_THREADS;  // first series of the next new batch
+    for (;;) {
+        // job 0: a new batch to K1; 1: 256 (or the last) from queue 0 to K2;
+        // 2: from queue 1 to the end.  A queue with 256 waiting goes first,
+        // so neither holds more than 511 entries.
+        int job;
+        if (qcnt[1] >= LB_THREADS)
+            job = 2;
+        else if (qcnt[0] >= LB_THREADS)
+            job = 1;
+        else if (next < nser)
+            job = 0;
+        else if (qcnt[0] > 0)
+            job = 1;
+        else if (qcnt[1] > 0)
+            job = 2;
+        else
+            break;
+        int cnt = 0, ka = 0, kb = a.k1, c = a.c_begin, n = 0;
+        bool valid;
+        float acc[QT];
+        if (job == 0) {
+            const int i = next + threadIdx.x;
+            valid = i < nser;
+            c = a.c_begin + (valid ? i : 0);
+            n = valid ? a.db_len[c] : 0;
+            lb_multi_init<QT>(a, mq, n, acc);
+            next += gridDim.x * LB_THREADS;
+        } else {
+            const int q = job - 1;
+            cnt = min(LB_THREADS, qcnt[q]);
+            valid = (int)threadIdx.x < cnt;
+            const float *qs = qmem + (size_t)q * LBQ_CAP * (QT + 1);
+            const int pos = (qhead[q] + (int)threadIdx.x) % LBQ_CAP;
+#pragma unroll
+            for (int j = 0; j < QT; ++j)
+                acc[j] = valid ? qs[(1 + j) * LBQ_CAP + pos] : KNN_INF;
+            if (valid) {
+                c = __float_as_int(qs[pos]);
+                n = a.db_len[c];
+            }
+            ka = q == 0 ? a.k1 : a.k2;
+            kb = q == 0 ? a.k2 : (1 << 30);
+        }
+        const int nch = (n + PPC - 1) / PPC;
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+        const int ke = min(kb, nch);
+        for (int ch = ka; ch < ke; ++ch) {
+            if (((ch - ka) & 3) == 0 && lb_all_over<QT>(acc, lim))
+                break;
+            st_points += (unsigned long long)PPC * nqt;
+            lb_multi_chunk<D, FORM, QT>(x4 + ch * F4, lo_s + ch * F4, hi_s + ch * F4, st4,
+                                        (ch + 1) * PPC <= n, ch * PPC, n, acc);
+        }
+        const bool done = !valid || nch <= kb || lb_all_over<QT>(acc, lim);
+        lb_multi_finish<QT>(a, q0, nqt, mq, lim, acc, valid && done, c, n, lane, st_pairs, st_inf,
+                            st_pruned);
+        if (job < 2) {
+            const bool push = valid && !done;
+            const unsigned pb = __ballot_sync(KNN_FULL_MASK, push);
+            int base = 0;
+            if (lane == 0 && pb)
+                base = atomicAdd(&qpush[job], __popc(pb));
+            base = __shfl_sync(KNN_FULL_MASK, base, 0);
+            if (push) {
+                const int pos = (qhead[job] + qcnt[job] + base + __popc(pb & ((1u << lane) - 1u))) %
+                                LBQ_CAP;
+                float *qd = qmem + (size_t)job * LBQ_CAP * (QT + 1);
+                qd[pos] = __int_as_float(c);
+#pragma unroll
+                for (int j = 0; j < QT; ++j)
+                    qd[(1 + j) * LBQ_CAP + pos] = acc[j];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (job >= 1) {
+                qhead[job - 1] = (qhead[job - 1] + cnt) % LBQ_CAP;
+                qcnt[job - 1] -= cnt;
+            }
+            if (job < 2) {
+                qcnt[job] += qpush[job];
+                qpush[job] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    lb_flush_stats(a, lane, st_pairs, st_inf, st_pruned, st_points);
+}
+
+size_t lb_queue_floats(int n_sm, int nq)
+{
+    // a launch has at most n_sm * 8 + query tiles CTAs (tile of 4 or more)
+    const size_t ctas = (size_t)n_sm * 8 + (size_t)(nq + 3) / 4;
+    return ctas * 2 * LBQ_CAP * 17;
 }
 
 // Bounded wait for the given phase parity of an mbarrier.
@@ -728,6 +895,10 @@ static void lb_attr_q()
                          200 * 1024);
     cudaFuncSetAttribute(lb_win_kernel<D, 0, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
+    cudaFuncSetAttribute(lb_compact_kernel<D, 0, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaFuncSetAttribute(lb_compact_kernel<D, 1, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     cudaFuncSetAttribute(lb_win_kernel<D, 1, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
 }
@@ -751,14 +922,37 @@ void lb_init_attributes()
 template <int D, int QT>
 static void lb_multi_launch(const LbArgs &a, int form, int n_sm, cudaStream_t st)
 {
+    constexpr int CH = chunk_floats(D);
     const size_t smem = (size_t)QT * a.env_floats * 4 * 2;
     const int nser = a.c_end - a.c_begin;
     const int qtiles = (a.nq + QT - 1) / QT;
-    int bx = (nser + LB_THREADS - 1) / LB_THREADS;
+    const int batches = (nser + LB_THREADS - 1) / LB_THREADS;
+    int bx = batches;
     const int want = (n_sm * 8 + qtiles - 1) / qtiles;
     bx = bx < want ? bx : want;
     if (bx < 1)
         bx = 1;
+    // compaction pays when a CTA walks several batches of long enough series
+    const int nch_env = a.env_floats / CH;
+    const bool compact = a.items && a.lbq && a.compact != 1 && nch_env >= 8 &&
+                         (a.compact == 2 || (nch_env >= 16 && batches >= 4 * bx));
+    if (compact) {
+        LbArgs c = a;
+        c.k1 = (nch_env / 4 + 3) / 4 * 4;
+        c.k2 = (nch_env / 2 + 3) / 4 * 4;
+        if (c.k1 < 4)
+            c.k1 = 4;
+        if (c.k2 <= c.k1)
+            c.k2 = c.k1 + 4;
+        if (a.compact == 2 && batches < 4 * bx)
+            bx = (batches + 3) / 4;  // several batches per CTA, so that queues fill
+        dim3 grid(bx, qtiles);
+        if (form == 0)
+            lb_compact_kernel<D, 0, QT><<<grid, LB_THREADS, smem, st>>>(c);
+        else
+            lb_compact_kernel<D, 1, QT><<<grid, LB_THREADS, smem, st>>>(c);
+        return;
+    }
     dim3 grid(bx, qtiles);
     if (form == 0)
         lb_multi_kernel<D, 0, QT><<<grid, LB_THREADS, smem, st>>>(a);

@@ -46,6 +46,7 @@ struct Workspace {
     DevBuf q_raw, q_src_off;            // staged caller queries (host input)
     DevBuf qbuf, q_off, q_len;          // repacked queries of the batch
     DevBuf q_order;                     // batch queries sorted by length (LB tiles)
+    DevBuf lbq;                         // LB_Box compaction queues (filter mode)
     DevBuf env_lo, env_hi;
     DevBuf thr, slots, ub_slots;
     DevBuf items, item_lb;
@@ -118,6 +119,7 @@ struct knn_db {
     bool tuning = false;                  // autotuner running: one DP segment per bucket
     int lb_qtile[2] = {0, 0};             // queries per LB pass per distance (0: 16)
     int lb_window[2] = {0, 0};            // LB envelope window in chunks (0: automatic)
+    int lb_compact[2] = {0, 0};           // LB compaction: 0 automatic, 1 never, 2 always
     std::vector<double> seg_ms;           // profile: DP time per segment of the last scan
     std::vector<int> seg_first_bucket;    // first bucket of each segment of the last scan
     ~knn_db()

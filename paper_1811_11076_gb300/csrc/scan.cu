@@ -183,6 +183,8 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(q_off, sizeof(int64_t) * nq);
     G_(q_len, sizeof(int) * nq);
     G_(q_order, sizeof(int) * nq);
+    if (!(pl.seeded && !pl.learned))
+        G_(lbq, sizeof(float) * lb_queue_floats(db->n_sm, nq));
     G_(env_lo, sizeof(float) * nq * pl.env_stride);
     G_(env_hi, sizeof(float) * nq * pl.env_stride);
     G_(thr, sizeof(float) * nq);
@@ -401,6 +403,8 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
                 l.skip = ws.skip.as<uint32_t>();
                 l.skip_words = (db->N + 31) / 32;
             }
+            l.lbq = ws.lbq.as<float>();
+            l.compact = db->lb_compact[kind];
             l.items = ws.items.as<int2>() + sg.base;
             l.item_lb = ws.item_lb.as<float>() + sg.base;
             l.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];

@@ -361,12 +361,13 @@ def test_lb_tiles_and_windows_give_identical_results(kw, kind, d, lengths, nq):
     band, k = 0.1, 4
     oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(band), kind=kind, k=k)
     db = kw.KnnDB(cuda(w.db), w.db_off)
-    assert db.get_lb_tile(kind) == (0, 0)
+    assert db.get_lb_tile(kind) == (0, 0, 0)
     ref = None
-    for qt in (4, 8, 16):
-        for win in (0, 1, 5, 64):
-            db.set_lb_tile(kind, qt, win)
-            assert db.get_lb_tile(kind) == (qt, win)
+    for qt, win, comp in [(q, w_, 0) for q in (4, 8, 16) for w_ in (0, 1, 5, 64)] + \
+            [(q, 0, c) for q in (4, 16) for c in (1, 2)]:
+        if True:
+            db.set_lb_tile(kind, qt, win, comp)
+            assert db.get_lb_tile(kind) == (qt, win, comp)
             for seed in (kw.SEED_GREEDY, kw.SEED_LB, kw.SEED_NONE):
                 ids, dist = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind, seed=seed)
                 ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
@@ -374,9 +375,35 @@ def test_lb_tiles_and_windows_give_identical_results(kw, kind, d, lengths, nq):
                 if ref is None:
                     ref = (ids, dist)
                 assert (ids == ref[0]).all() and (dist == ref[1]).all()
-    for bad in ((kind, 5, 0), (kind, 16, -1), (2, 16, 0)):
+    for bad in ((kind, 5, 0, 0), (kind, 16, -1, 0), (2, 16, 0, 0), (kind, 16, 0, 3)):
         with pytest.raises(kw.KnnError):
             db.set_lb_tile(*bad)
+    db.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_lb_compaction_gives_identical_results(kw, kind):
+    """The compacting LB_Box kernel (survivor queues between checkpoints) must
+    bound and queue exactly as the plain one: one bucket of 5,000 series, so
+    that CTAs walk several batches and the queues fill past 256 entries; with
+    no seed threshold (every series survives every checkpoint) and with one."""
+    w = make_workload(n_series=5000, n_queries=24, d=3, length=128, n_classes=6, seed=41)
+    band, k = 0.1, 5
+    oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(band), kind=kind, k=k)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    ref = None
+    for comp in (1, 2, 0):
+        for qt in (16, 8):
+            db.set_lb_tile(kind, qt, 0, comp)
+            for seed in (kw.SEED_NONE, kw.SEED_GREEDY):
+                ids, dist, st = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind,
+                                        seed=seed, stats=True)
+                ids, dist = ids.cpu().numpy(), dist.cpu().numpy()
+                check_knn(ids, dist, oids, odist, kind, k)
+                if ref is None:
+                    ref = (ids, dist)
+                assert (ids == ref[0]).all() and (dist == ref[1]).all()
+                assert st["pairs"] == 24 * 5000
     db.close()
 
 
