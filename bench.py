@@ -61,7 +61,11 @@ TRAIN_PAIRS = 200_000
 # workloads, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
 # captures of the current kernels (the summaries in profiles/ give the commands).
 # A kernel changed since its capture has no entry (traffic null).
-TRAFFIC = {}
+TRAFFIC = {
+    # mean of the DTW and DK launches of one 1,000-query scan
+    ("lb_compact_kernel", "scale_d3_n100k_L256"): 5.883e9,
+    ("dp_kernel", "scale_d3_n100k_L256"): 2.201e9,
+}
 
 
 def peaks():
@@ -148,11 +152,16 @@ def workload(world: int):
     return make_workload(**kw)
 
 
-def cpu_baseline(w, n_sample: int = 4) -> dict:
-    """The FP64 oracle (paper's pruned scan) on a bounded sample of queries."""
+def cpu_baseline(w, n_sample: int = 0) -> dict:
+    """The FP64 oracle (paper's pruned scan) on a bounded sample of queries.
+
+    The oracle runs one query per thread, so the sample is one query per host
+    core (n_sample = 0) and `cores` is the number of threads that worked."""
     import oracle
     oracle.lib()
-    cores = os.cpu_count() or 1
+    n_sample = n_sample or (os.cpu_count() or 1)
+    n_sample = min(n_sample, int(w.q_off.shape[0] - 1))
+    cores = min(os.cpu_count() or 1, n_sample)
     band = float(np.float32(BAND))
     q_off = w.q_off[: n_sample + 1]
     q = w.q[: q_off[-1]]
@@ -175,7 +184,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = workload(1)
-    n_sample = 2
+    # one query per host core per step (the oracle runs a query per thread)
+    cores = os.cpu_count() or 1
+    n_sample = min(args.cpu_sample or cores, N_QUERIES)
+    cores = min(cores, n_sample)
     for _ in range(args.warmup):
         cpu_baseline(w, n_sample)
     t0 = time.perf_counter()
@@ -183,7 +195,6 @@ def run_reference(args):
         cpu_baseline(w, n_sample)
     dt = time.perf_counter() - t0
     value = 2 * n_sample * args.steps / dt
-    cores = os.cpu_count() or 1
     sample = f"{n_sample} queries x {N_SERIES} series per step, DTW and DK, k={K}, band 10%"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -356,15 +367,16 @@ def run_gpu(args):
             r_["frac_at_sampled_clock"] = achieved / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
         return r_
 
-    # the library stages a tile's whole envelopes when 16 of them fit in
-    # 192 KB of shared memory (lb_multi_kernel), else windows (lb_win_kernel)
-    deff = D if D <= 8 else 16
-    ch = deff * 4 // math.gcd(deff, 4)
-    longest = LENGTH or int(np.diff(w.db_off).max())
-    shortest = LENGTH or int(np.diff(w.db_off).min())
-    env_bytes = [-(-n_ // (ch // deff)) * ch * 8 * 16 for n_ in (shortest, longest)]
-    lb_name = ("lb_multi_kernel" if env_bytes[1] <= 192 * 1024 else
-               "lb_win_kernel" if env_bytes[0] > 192 * 1024 else "lb_multi_kernel+lb_win_kernel")
+    # which LB_Box kernels ran (the library reports a bit mask per scan)
+    lb_bits = 0
+    for _, s in collected:
+        lb_bits |= int(s.get("lb_kernels", 0))
+    if graph:
+        for _, s in prof:
+            lb_bits |= int(s.get("lb_kernels", 0))
+    lb_name = "+".join(n_ for b_, n_ in ((1, "lb_kernel"), (2, "lb_multi_kernel"),
+                                         (4, "lb_win_kernel"), (8, "lb_compact_kernel"))
+                       if lb_bits & b_) or "lb_multi_kernel"
     stage_roofs = {"lb": alu_roof(lb_name, lb_ops, stage["lb"]),
                    "dp": alu_roof("dp_kernel", dp_ops, stage["dp"])}
     dominant = "lb" if stage["lb"] >= stage["dp"] else "dp"
@@ -468,7 +480,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=4)
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="queries of the oracle's timed sample (0: one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
     ap.add_argument("--no-variants", action="store_true")

@@ -124,6 +124,9 @@ typedef struct {
     double ms_lb;            /* profile = 1: envelopes + LB_Box stream           */
     double ms_dp;            /* profile = 1: banded dynamic programs             */
     double ms_finalize;      /* profile = 1: FP64 re-scoring and output          */
+    int64_t lb_kernels;      /* LB_Box kernels that ran, bit mask: 1 one query per
+                                pass, 2 whole envelopes, 4 windowed envelopes,
+                                8 whole envelopes with compaction              */
 } knn_stats;
 
 typedef struct knn_db knn_db;

@@ -75,7 +75,7 @@ class Stats(C.Structure):
                 ("dp_calls", C.c_int64), ("dp_abandoned", C.c_int64), ("dp_cells", C.c_int64),
                 ("reranked", C.c_int64), ("lb_points", C.c_int64), ("launches", C.c_int64), ("ms_total", C.c_double),
                 ("ms_seed", C.c_double), ("ms_lb", C.c_double), ("ms_dp", C.c_double),
-                ("ms_finalize", C.c_double)]
+                ("ms_finalize", C.c_double), ("lb_kernels", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

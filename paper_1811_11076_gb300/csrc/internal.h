@@ -246,6 +246,7 @@ enum Stat : int {
     STAT_RERANKED,
     STAT_SEED_CELLS,
     STAT_LB_POINTS,      // (query, series point) pairs bounded by LB_Box
+    STAT_LB_KERNELS,     // bit mask of the LB_Box kernels that ran (knn_stats.lb_kernels)
     STAT_COUNT
 };
 

@@ -146,6 +146,7 @@ __device__ __forceinline__ void lb_chunk(const float4 (&xv)[F4], const float4 *l
 template <int D, int FORM>
 __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
 {
+    lb_mark(a, 1ull);
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
     constexpr int F4 = CH / 4;
@@ -374,6 +375,13 @@ __device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float 
     return all_over;
 }
 
+// Record which LB_Box kernel ran (bit of knn_stats.lb_kernels), once per launch.
+__device__ __forceinline__ void lb_mark(const LbArgs &a, unsigned long long bit)
+{
+    if (a.stats && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        atomicOr(a.stats + STAT_LB_KERNELS, bit);
+}
+
 // Query of slot j of the tile starting at q0 (tiles follow the length order).
 __device__ __forceinline__ int lb_qslot(const LbArgs &a, int q0, int j)
 {
@@ -514,6 +522,7 @@ __device__ __forceinline__ void lb_flush_stats(const LbArgs &a, int lane, unsign
 template <int D, int FORM, int QT>
 __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
 {
+    lb_mark(a, 2ull);
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
     constexpr int F4 = CH / 4;
@@ -601,6 +610,7 @@ constexpr int LBQ_CAP = 512;  // entries per queue: < 256 waiting + 256 arriving
 template <int D, int FORM, int QT>
 __global__ void __launch_bounds__(LB_THREADS, 2) lb_compact_kernel(const LbArgs a)
 {
+    lb_mark(a, 8ull);
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
     constexpr int F4 = CH / 4;
@@ -781,6 +791,7 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
 template <int D, int FORM, int QT>
 __global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
 {
+    lb_mark(a, 4ull);
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
     constexpr int F4 = CH / 4;

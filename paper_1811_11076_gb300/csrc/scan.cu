@@ -806,6 +806,7 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         stats->ms_lb = stage_ms[1];
         stats->ms_dp = stage_ms[2];
         stats->ms_finalize = stage_ms[3];
+        stats->lb_kernels = (int64_t)hc.stats[STAT_LB_KERNELS];
     }
     if (hc.status & KNN_DEV_TIMEOUT)
         return set_error(KNN_ERR_TIMEOUT, "a device wait gave up");
