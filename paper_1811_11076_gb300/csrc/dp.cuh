@@ -24,16 +24,16 @@
 // the band get +inf through the FMA accumulator of their cost (mask 0/inf).
 //
 // Start and end.  Every pair is swept in whole blocks of U steps, and the
-// sweep starts at a step s_start <= 0 chosen so that the end cell
+// sweep starts at a step s_start in (-U, 0] chosen so that the end cell
 // (m-1, n-1) falls on the last step of a block; the result is then read once
 // per block, outside the unrolled loop.  The steps before 0 run over a
 // virtual prefix: rows i < 0 and columns j < 0 read a sentinel point of huge
 // coordinates, so a cell with both indices negative costs exactly 0 and a
-// cell with one negative index costs about 1e36 (or +inf).  With every
-// in-band cell of the first step in the negative quadrant and set to 0,
-// cell (0,0) receives min(...) = 0 from (-1,-1) and every real cell receives
-// the same value as in the plain recurrence (the prefix can only reach it
-// through (0,0)).
+// cell with one negative index costs about 1e36 (or +inf).  The two
+// anti-diagonals before the first step start as 0 where both indices are
+// negative and +inf elsewhere, so cell (0,0) receives min(...) = 0 from
+// (-1,-1) and every real cell receives the same value as in the plain
+// recurrence (the prefix can only reach it through (0,0)).
 //
 // Early abandoning (Section 4, first paragraph; Algorithm 3's empty active
 // set for DK): the last two anti-diagonals form a cut of every warping path,
@@ -148,24 +148,29 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                         r = band_radius(m, n, a.band);
                         const int lo = -(r + (r & 1));
                         h = lo / 2 + P * lam;
+                        s_f = (m + n - 2) >> 1;
+                        // a whole number of U-step blocks from s0 <= 0 up to s_f
+                        const int nsteps = (s_f + 1 + U - 1) / U * U;
+                        s0 = s_f - nsteps + 1;
+                        // state before step s0: anti-diagonals 2s0-2 (E) and
+                        // 2s0-1 (O), all cells with i + j < 0; a cell with both
+                        // indices negative is 0, one with a single negative
+                        // index (or outside the band) +inf
 #pragma unroll
                         for (int e = 0; e < P; ++e) {
                             const int de = lo + 2 * P * lam + 2 * e;
                             mE[e] = (abs(de) <= r) ? 0.f : KNN_INF;
                             mO[e] = (abs(de + 1) <= r) ? 0.f : KNN_INF;
-                            E[e] = mE[e];  // virtual prefix: in-band cells are 0
-                            O[e] = mO[e];
+                            const int te = 2 * s0 - 2, to = 2 * s0 - 1;
+                            const bool ze = te - de < 0 && te + de < 0;       // 2i, 2j < 0
+                            const bool zo = to - de - 1 < 0 && to + de + 1 < 0;
+                            E[e] = ze ? mE[e] : KNN_INF;
+                            O[e] = zo ? mO[e] : KNN_INF;
                         }
                         const int off = (n - m) - lo;
                         fin_lane = off / (2 * P);
                         fin_slot = (off % (2 * P)) >> 1;
                         fin_odd = off & 1;
-                        s_f = (m + n - 2) >> 1;
-                        // first step: all in-band cells in the negative quadrant,
-                        // and a whole number of U-step blocks up to s_f
-                        const int smin = -((r + 1) >> 1) - 1;
-                        const int nsteps = (s_f - smin + 1 + U - 1) / U * U;
-                        s0 = s_f - nsteps + 1;
 #pragma unroll
                         for (int p = 0; p < U; ++p) {
                             load_point_prefix<D>(qp, s0 - h - ((U - p) % U), m - 1, qw[p]);

@@ -61,6 +61,13 @@ void launch_envelope(const EnvArgs &a, cudaStream_t st)
     envelope_kernel<<<grid, threads, 0, st>>>(a);
 }
 
+// Record which LB_Box kernel ran (bit of knn_stats.lb_kernels), once per launch.
+__device__ __forceinline__ void lb_mark(const LbArgs &a, unsigned long long bit)
+{
+    if (a.stats && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        atomicOr(a.stats + STAT_LB_KERNELS, bit);
+}
+
 // ---------------------------------------------------------------------------
 // TMA bulk copy global -> shared, completion tracked by an mbarrier
 
@@ -373,13 +380,6 @@ __device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float 
     for (int j = 0; j < QT; ++j)
         all_over &= acc[j] > lim[j];
     return all_over;
-}
-
-// Record which LB_Box kernel ran (bit of knn_stats.lb_kernels), once per launch.
-__device__ __forceinline__ void lb_mark(const LbArgs &a, unsigned long long bit)
-{
-    if (a.stats && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-        atomicOr(a.stats + STAT_LB_KERNELS, bit);
 }
 
 // Query of slot j of the tile starting at q0 (tiles follow the length order).
