@@ -61,11 +61,7 @@ TRAIN_PAIRS = 200_000
 # workloads, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
 # captures of the current kernels (the summaries in profiles/ give the commands).
 # A kernel changed since its capture has no entry (traffic null).
-TRAFFIC = {
-    # mean of the DTW and DK launches of one 1,000-query scan
-    ("lb_compact_kernel", "scale_d3_n100k_L256"): 5.883e9,
-    ("dp_kernel", "scale_d3_n100k_L256"): 2.201e9,
-}
+TRAFFIC = {}
 
 
 def peaks():

@@ -267,7 +267,8 @@ KNN_API knn_status knn_pairwise(const float *a, const int64_t *a_off, const floa
  * inside the library, present on every device that loads it until exit.
  * Limits: n_pairs <= 65536; 1 <= n_a, n_b <= 16384 series per set; after
  * padding each series to whole chunks of lcm(d', 4) floats (d' = d, or 16
- * for 9 <= d <= 16) at most 1,048,576 floats per set; max_len (an upper bound
+ * for 9 <= d <= 16), plus one chunk per series, at most 1,048,576 floats
+ * per set; max_len (an upper bound
  * on every series length, used to choose the DP shape) <= 65536.  Larger
  * inputs are rejected (KNN_ERR_INVALID for counts, KNN_ERR_CAPACITY for the
  * padded sizes) and nothing is computed.  All pointers are device memory;

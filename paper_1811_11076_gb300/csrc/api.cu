@@ -276,6 +276,7 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
         const int n = (int)(hoff[id + 1] - hoff[id]);
         db->h_len[c] = n;
         db->h_len_by_id[id] = n;
+        total += CH;  // leading chunk: the DP's sentinel point
         doff[c] = total;
         doff_by_id[id] = total;
         total += (int64_t)((n + PPC - 1) / PPC) * CH;
@@ -347,7 +348,7 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
         return set_error(KNN_ERR_INVALID, "database contains NaN or Inf");
     }
     launch_repack(src, (const int64_t *)off_stage.p, (const int *)db->id.p, N, d, deff,
-                  (const int64_t *)db->off.p, (float *)db->data.p, st);
+                  (const int64_t *)db->off.p, (float *)db->data.p, st, true);
     e = cudaStreamSynchronize(st);
     if (e == cudaSuccess)
         e = cudaGetLastError();

@@ -17,6 +17,12 @@ enum : int {
     KNN_DEV_BAD_SHAPE = 4,   // a launch received a shape it cannot handle
 };
 
+// Coordinate of the sentinel point stored before every series and query the
+// DP reads (the chunk of floats before its first point): a row or column
+// index below 0 reads it, so a cell with both indices negative costs 0 and a
+// cell with one negative index about 1e36 per coordinate.
+#define KNN_DP_SENTINEL 1e18f
+
 // Upper limit on polling iterations of any device-side wait; with the
 // backoff below this is of the order of a second.
 #define KNN_SPIN_LIMIT (1u << 22)

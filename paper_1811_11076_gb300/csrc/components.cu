@@ -48,7 +48,7 @@ knn_status stage_one_query(knn_db *db, const float *query, int64_t m, cudaStream
     if (!ok)
         return set_error(KNN_ERR_INVALID, "query contains NaN or Inf");
     launch_repack(ws.q_raw.as<float>(), ws.q_src_off.as<int64_t>(), nullptr, 1, db->d, db->deff,
-                  ws.q_off.as<int64_t>(), ws.qbuf.as<float>(), st);
+                  ws.q_off.as<int64_t>(), ws.qbuf.as<float>(), st, false);
     int64_t env = 0;
     for (auto &b : db->buckets)
         env = std::max<int64_t>(env, (int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
@@ -288,11 +288,13 @@ extern "C" knn_status knn_pairwise(const float *a, const int64_t *a_off, const f
         int64_t ta = 0, tb = 0;
         for (int64_t i = 0; i < na; ++i) {
             la[i] = (int)(hao[i + 1] - hao[i]);
+            ta += CH;  // leading chunk: the DP's sentinel point
             ra[i] = ta;
             ta += (int64_t)((la[i] + PPC - 1) / PPC) * CH;
         }
         for (int64_t i = 0; i < nb; ++i) {
             lb[i] = (int)(hbo[i + 1] - hbo[i]);
+            tb += CH;
             rb[i] = tb;
             tb += (int64_t)((lb[i] + PPC - 1) / PPC) * CH;
             ida[i] = (int)i;
@@ -310,8 +312,8 @@ extern "C" knn_status knn_pairwise(const float *a, const int64_t *a_off, const f
         cudaMemcpyAsync(BL.p, lb.data(), 4 * nb, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(BID.p, ida.data(), 4 * nb, cudaMemcpyHostToDevice, st);
         cudaMemsetAsync(CT.p, 0, sizeof(Ctrl), st);
-        launch_repack(a, a_off, nullptr, (int)na, d, deff, AO.as<int64_t>(), A.as<float>(), st);
-        launch_repack(b, b_off, nullptr, (int)nb, d, deff, BO.as<int64_t>(), B.as<float>(), st);
+        launch_repack(a, a_off, nullptr, (int)na, d, deff, AO.as<int64_t>(), A.as<float>(), st, true);
+        launch_repack(b, b_off, nullptr, (int)nb, d, deff, BO.as<int64_t>(), B.as<float>(), st, true);
         pairs_to_items<<<256, 256, 0, st>>>(pa, pb, n_pairs, IT.as<int2>(), ILB.as<float>());
         Ctrl *ct = CT.as<Ctrl>();
         const int np = (int)n_pairs;

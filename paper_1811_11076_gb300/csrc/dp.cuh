@@ -50,20 +50,13 @@
 namespace knn {
 
 constexpr int DP_THREADS = 128;
-constexpr float DP_PREFIX = 1e18f;  // sentinel coordinate of the virtual prefix
-
-// Point idx of a series (clamped to its last point), or the sentinel point
-// for idx < 0.
+// Point idx of a series, clamped to [-1, last]: index -1 is the sentinel
+// point stored in the chunk before every series and query the DP reads.
 template <int D>
 __device__ __forceinline__ void load_point_prefix(const float *p, int idx, int last,
                                                   float (&v)[D])
 {
-    load_point<D>(p + clampi(idx, 0, last) * D, v);
-    if (idx < 0) {
-#pragma unroll
-        for (int k = 0; k < D; ++k)
-            v[k] = DP_PREFIX;
-    }
+    load_point<D>(p + clampi(idx, -1, last) * D, v);
 }
 
 template <int D, int P, int KIND>

@@ -978,8 +978,9 @@ extern "C" knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_
         cudaMemcpy(sample.data(), db->data.p, 4 * ns, cudaMemcpyDeviceToHost);
         double sum = 0, sq = 0;
         int64_t cnt = 0;
+        // zeros are padding, the 1e18 values the DP's sentinel chunks
         for (float v : sample)
-            if (v != 0.f) {
+            if (v != 0.f && fabsf(v) < 0.5f * KNN_DP_SENTINEL) {
                 sum += v;
                 sq += (double)v * v;
                 ++cnt;

@@ -226,9 +226,11 @@ void launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cud
 void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st);
 // Copy series order[c] of `src` (d floats per point, point offsets
 // src_off) to dst + dst_off[c] with deff floats per point (extra coordinates
-// zero) and zero padding up to the chunk-padded size.
+// zero) and zero padding up to the chunk-padded size.  dp_lead: the chunk of
+// floats before each series (reserved by the caller's offsets) is filled
+// with KNN_DP_SENTINEL, the point the DP reads for negative indices.
 void launch_repack(const float *src, const int64_t *src_off, const int *order, int nser, int d,
-                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st);
+                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st, bool dp_lead);
 // dst[q][id[c]] = src[q][c] for c < n (bucket order -> caller order).
 void launch_scatter_by_id(const float *src, const int *db_id, int n, int nq, int64_t src_stride,
                           float *dst, int64_t dst_stride, int out_sqrt, cudaStream_t st);

@@ -298,17 +298,13 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
 // points carries at most CH/2 + 2 + n roundings in the sum form (d in the
 // max form).
 template <int D, int FORM, int QT>
-__device__ __forceinline__ void lb_multi_chunk(const float4 *__restrict__ x4c, const float4 *lo,
-                                               const float4 *hi, int qstride4, bool full,
-                                               int p_first, int n, float (&acc)[QT])
+__device__ __forceinline__ void lb_multi_chunk(const float4 (&xv)[chunk_floats(D) / 4],
+                                               const float4 *lo, const float4 *hi, int qstride4,
+                                               bool full, int p_first, int n, float (&acc)[QT])
 {
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
     constexpr int F4 = CH / 4;
-    float4 xv[F4];
-#pragma unroll
-    for (int f = 0; f < F4; ++f)
-        xv[f] = __ldg(x4c + f);
 #pragma unroll
     for (int j = 0; j < QT; ++j) {
         // e = distance of every element to its box, max(l - x, x - u, 0)
@@ -380,6 +376,43 @@ __device__ __forceinline__ bool lb_all_over(const float (&acc)[QT], const float 
     for (int j = 0; j < QT; ++j)
         all_over &= acc[j] > lim[j];
     return all_over;
+}
+
+// Chunks [ka, ke) of one series against the tile's envelopes (chunk ch of
+// the envelopes at lo/hi + (ch - cbase) * F4), the next chunk's load in
+// flight while the current one is bounded; with `abandon`, stops once every
+// bound exceeds its limit (checked every 4 chunks).
+template <int D, int FORM, int QT>
+__device__ __forceinline__ void lb_run_chunks(const float4 *__restrict__ x4, const float4 *lo,
+                                              const float4 *hi, int cbase, int st4, int ka, int ke,
+                                              int n, int nqt, bool abandon, const float *lim,
+                                              float (&acc)[QT], unsigned long long &st_points)
+{
+    constexpr int CH = chunk_floats(D);
+    constexpr int PPC = chunk_points(D);
+    constexpr int F4 = CH / 4;
+    if (ka >= ke)
+        return;
+    float4 nx[F4];
+#pragma unroll
+    for (int f = 0; f < F4; ++f)
+        nx[f] = __ldg(x4 + ka * F4 + f);
+    for (int ch = ka; ch < ke; ++ch) {
+        if (abandon && ((ch - ka) & 3) == 0 && lb_all_over<QT>(acc, lim))
+            break;
+        float4 xv[F4];
+#pragma unroll
+        for (int f = 0; f < F4; ++f)
+            xv[f] = nx[f];
+        if (ch + 1 < ke) {
+#pragma unroll
+            for (int f = 0; f < F4; ++f)
+                nx[f] = __ldg(x4 + (ch + 1) * F4 + f);
+        }
+        st_points += (unsigned long long)PPC * nqt;
+        lb_multi_chunk<D, FORM, QT>(xv, lo + (ch - cbase) * F4, hi + (ch - cbase) * F4, st4,
+                                    (ch + 1) * PPC <= n, ch * PPC, n, acc);
+    }
 }
 
 // Query of slot j of the tile starting at q0 (tiles follow the length order).
@@ -580,16 +613,11 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
         lb_multi_init<QT>(a, mq, n, acc);
         const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
         const int nch = (n + PPC - 1) / PPC;
-        for (int ch = 0; ch < nch; ++ch) {
-            // early abandoning of the bound (Section 4): partial sums and
-            // maxima only grow, so once all exceed their limits the series
-            // is pruned for every query of the tile
-            if (a.items && (ch & 3) == 0 && lb_all_over<QT>(acc, lim))
-                break;
-            st_points += (unsigned long long)PPC * nqt;
-            lb_multi_chunk<D, FORM, QT>(x4 + ch * F4, lo_s + ch * F4, hi_s + ch * F4, st4,
-                                        (ch + 1) * PPC <= n, ch * PPC, n, acc);
-        }
+        // early abandoning of the bound (Section 4): partial sums and maxima
+        // only grow, so once all exceed their limits the series is pruned for
+        // every query of the tile
+        lb_run_chunks<D, FORM, QT>(x4, lo_s, hi_s, 0, st4, 0, nch, n, nqt, a.items != nullptr, lim,
+                                   acc, st_points);
         lb_multi_finish<QT>(a, q0, nqt, mq, lim, acc, valid, c, n, lane, st_pairs, st_inf,
                             st_pruned);
     }
@@ -712,13 +740,8 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_compact_kernel(const LbArgs 
         const int nch = (n + PPC - 1) / PPC;
         const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
         const int ke = min(kb, nch);
-        for (int ch = ka; ch < ke; ++ch) {
-            if (((ch - ka) & 3) == 0 && lb_all_over<QT>(acc, lim))
-                break;
-            st_points += (unsigned long long)PPC * nqt;
-            lb_multi_chunk<D, FORM, QT>(x4 + ch * F4, lo_s + ch * F4, hi_s + ch * F4, st4,
-                                        (ch + 1) * PPC <= n, ch * PPC, n, acc);
-        }
+        lb_run_chunks<D, FORM, QT>(x4, lo_s, hi_s, 0, st4, ka, ke, n, nqt, true, lim, acc,
+                                   st_points);
         const bool done = !valid || nch <= kb || lb_all_over<QT>(acc, lim);
         lb_multi_finish<QT>(a, q0, nqt, mq, lim, acc, valid && done, c, n, lane, st_pairs, st_inf,
                             st_pruned);
@@ -866,13 +889,8 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_win_kernel(const LbArgs a)
         const float4 *hi_w = lo_w + QT * wst4;
         const int cb = w * WCH;
         const int ce = min(cb + WCH, nch);
-        for (int ch = cb; ch < ce; ++ch) {
-            if (a.items && ((ch - cb) & 3) == 0 && lb_all_over<QT>(acc, lim))
-                break;
-            st_points += (unsigned long long)PPC * nqt;
-            lb_multi_chunk<D, FORM, QT>(x4 + ch * F4, lo_w + (ch - cb) * F4, hi_w + (ch - cb) * F4,
-                                        wst4, (ch + 1) * PPC <= n, ch * PPC, n, acc);
-        }
+        lb_run_chunks<D, FORM, QT>(x4, lo_w, hi_w, cb, wst4, cb, ce, n, nqt, a.items != nullptr, lim,
+                                   acc, st_points);
         const bool finished = nch <= cb + WCH || (a.items && lb_all_over<QT>(acc, lim));
         // every thread is done with buffer w & 1 after this barrier
         const bool all_finished = __syncthreads_and(finished);

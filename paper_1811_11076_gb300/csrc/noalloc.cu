@@ -121,7 +121,7 @@ __device__ void na_offsets(const int64_t *off, int n, int max_len, int ppc, int 
         if (L < 1 || L > max_len)
             atomicOr(flag, NA_BAD_LENGTH);
         const int64_t Lc = L < 1 ? 1 : (L > max_len ? max_len : L);
-        sum += (Lc + ppc - 1) / ppc * chf;
+        sum += chf + (Lc + ppc - 1) / ppc * chf;  // sentinel chunk + the series
     }
     part[t] = sum;
     __syncthreads();
@@ -139,6 +139,7 @@ __device__ void na_offsets(const int64_t *off, int n, int max_len, int ppc, int 
     for (int s = s0; s < s1; ++s) {
         const int64_t L = off[s + 1] - off[s];
         const int64_t Lc = L < 1 ? 1 : (L > max_len ? max_len : L);
+        acc += chf;  // leading chunk: the DP's sentinel point
         roff[s] = acc;
         rlen[s] = (int)Lc;
         acc += (Lc + ppc - 1) / ppc * chf;
@@ -196,6 +197,8 @@ __global__ void na_fill_kernel(NaPtrs p, const float *a, const int64_t *a_off, i
         const int n = is_a ? p.a_len[t] : p.b_len[t];
         float *dst = is_a ? p.a + p.a_off[t] : p.b + p.b_off[t];
         const int64_t total = (int64_t)((n + ppc - 1) / ppc) * chf;
+        for (int f = lane; f < chf; f += 32)
+            dst[f - chf] = KNN_DP_SENTINEL;
         for (int64_t f = lane; f < total; f += 32) {
             const int64_t i = f / deff;
             const int j = (int)(f - i * deff);
@@ -295,7 +298,7 @@ extern "C" knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off,
     if (status & NA_TOO_LARGE)
         return set_error(KNN_ERR_CAPACITY,
                          "series exceed the fixed scratch (1,048,576 floats per set after "
-                         "padding each series to whole chunks)");
+                         "padding each series to whole chunks, plus one chunk per series)");
     if (status)
         return set_error(KNN_ERR_CUDA, "device status set by the DP kernel");
     return KNN_OK;

@@ -86,6 +86,7 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
     for (int i = 0; i < nq; ++i) {
         const int m = (int)(hq_off[q0 + i + 1] - hq_off[q0 + i]);
         pl.m[i] = m;
+        pl.qfloats += CH;  // leading chunk: the DP's sentinel point
         pl.qoff[i] = pl.qfloats;
         pl.qfloats += (int64_t)((m + PPC - 1) / PPC) * CH;
         pl.max_m = std::max(pl.max_m, m);
@@ -279,7 +280,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     unsigned long long *stats = ctrl->stats;
 
     launch_repack(q_src, q_src_off, nullptr, nq, db->d, db->deff, ws.q_off.as<int64_t>(),
-                  ws.qbuf.as<float>(), st);
+                  ws.qbuf.as<float>(), st, true);
     cudaMemsetAsync(&ctrl->rer_count, 0, offsetof(Ctrl, stats) - offsetof(Ctrl, rer_count), st);
     launch_fill_f32(ws.thr.as<float>(), p.k > 0 ? KNN_INF_HOST : pl.eps_int, nq, st);
     launches += 2;

@@ -40,7 +40,7 @@ void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st)
 
 // One warp per series.
 __global__ void repack_kernel(const float *src, const int64_t *src_off, const int *order, int nser,
-                              int d, int deff, const int64_t *dst_off, float *dst)
+                              int d, int deff, const int64_t *dst_off, float *dst, int lead)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -54,6 +54,8 @@ __global__ void repack_kernel(const float *src, const int64_t *src_off, const in
         const int64_t total = (int64_t)((n + ppc - 1) / ppc) * chf;
         const float *sp = src + b * d;
         float *dp = dst + dst_off[c];
+        for (int f = lane; f < lead; f += 32)
+            dp[f - lead] = KNN_DP_SENTINEL;
         for (int64_t f = lane; f < total; f += 32) {
             const int64_t i = f / deff;
             const int j = (int)(f - i * deff);
@@ -63,14 +65,15 @@ __global__ void repack_kernel(const float *src, const int64_t *src_off, const in
 }
 
 void launch_repack(const float *src, const int64_t *src_off, const int *order, int nser, int d,
-                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st)
+                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st, bool dp_lead)
 {
     if (nser <= 0)
         return;
     int blocks = (nser + 7) / 8;
     if (blocks > 8192)
         blocks = 8192;
-    repack_kernel<<<blocks, 256, 0, st>>>(src, src_off, order, nser, d, deff, dst_off, dst);
+    repack_kernel<<<blocks, 256, 0, st>>>(src, src_off, order, nser, d, deff, dst_off, dst,
+                                          dp_lead ? chunk_floats(deff) : 0);
 }
 
 __global__ void scatter_kernel(const float *src, const int *db_id, int n, int64_t src_stride,
