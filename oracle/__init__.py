@@ -64,6 +64,13 @@ def lib():
             L.orc_greedy.restype = C.c_double
             L.orc_greedy.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int64,
                                      C.c_double, C.c_int]
+            L.orc_sub_distance.restype = C.c_double
+            L.orc_sub_distance.argtypes = [C.c_int, _d, C.c_int64, _d, C.c_int64, C.c_int, _i64]
+            L.orc_sub_sparse_dk.restype = C.c_double
+            L.orc_sub_sparse_dk.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_double,
+                                            _i64, _i64]
+            L.orc_sub_gdk.restype = C.c_double
+            L.orc_sub_gdk.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_double, _i64]
             for name in ("orc_sparse_dk", "orc_dtw_abandon"):
                 f = getattr(L, name)
                 f.restype = C.c_double
@@ -166,6 +173,32 @@ def sparse_dk(s, t, r: int, eps: float):
     cells = C.c_int64(0)
     v = lib().orc_sparse_dk(_p(s), m, _p(t), n, d, r, eps, C.byref(cells))
     return v, cells.value
+
+
+def sub_distance(kind: int, s, t):
+    """Subsequence search, plain definition (free-start/free-end DP, no band):
+    min over subsequences T[a..b] of DTW (kind 0, sum of squared costs) or DK
+    (kind 1, Euclidean) of S against T[a..b].  Returns (value, end b)."""
+    s, t, m, n, d = _pair_args(s, t)
+    end = C.c_int64(-1)
+    v = lib().orc_sub_distance(kind, _p(s), m, _p(t), n, d, C.byref(end))
+    return v, end.value
+
+
+def sub_sparse_dk(s, t, eps: float):
+    """Algorithm 3 with SUB = true; returns (value or +inf above eps, end, cells)."""
+    s, t, m, n, d = _pair_args(s, t)
+    end, cells = C.c_int64(-1), C.c_int64(0)
+    v = lib().orc_sub_sparse_dk(_p(s), m, _p(t), n, d, eps, C.byref(end), C.byref(cells))
+    return v, end.value, cells.value
+
+
+def sub_gdk(s, t, eps: float = float("inf")):
+    """Greedy dog-keeper for subsequence search (Algorithm 2); returns (bound, end)."""
+    s, t, m, n, d = _pair_args(s, t)
+    end = C.c_int64(-1)
+    v = lib().orc_sub_gdk(_p(s), m, _p(t), n, d, eps, C.byref(end))
+    return v, end.value
 
 
 def dtw_abandon(s, t, r: int, eps: float):

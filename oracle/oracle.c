@@ -369,6 +369,180 @@ double orc_sparse_dk(const double *s, int64_t m, const double *t, int64_t n, int
     return result <= eps ? result : ORC_INF;
 }
 
+/* ----------------------------------------------------------------------- */
+/* Subsequence search (Section 4.1 Algorithm 2, Section 4.2 Algorithm 3 with  */
+/* SUB = true): the query S (m points) against every subsequence T[a..b] of a */
+/* long series T (n points), no band.                                         */
+
+/* Plain definition by the free-start, free-end dynamic program: row 0 of
+ * every column starts a match (its value is its own cost), rows above follow
+ * the DTW or DK recursion of Section 2.1, and the result is the minimum of the
+ * last row over all columns, i.e. min over a <= b of DTW(S, T[a..b]) (sum of
+ * squared costs) or DK(S, T[a..b]) (max of Euclidean costs).  *end receives
+ * the smallest end column b of a minimum. */
+double orc_sub_distance(int kind, const double *s, int64_t m, const double *t, int64_t n, int d,
+                        int64_t *end)
+{
+    if (end)
+        *end = -1;
+    if (m <= 0 || n <= 0)
+        return ORC_INF;
+    double *prev = malloc(sizeof(double) * (size_t)m); /* column k-1 */
+    double *cur = malloc(sizeof(double) * (size_t)m);  /* column k   */
+    for (int64_t i = 0; i < m; ++i)
+        prev[i] = ORC_INF;
+    double best = ORC_INF;
+    for (int64_t k = 0; k < n; ++k) {
+        for (int64_t i = 0; i < m; ++i) {
+            const double c = kind == ORC_DTW ? sqdist(s + i * d, t + k * d, d)
+                                             : eucl(s + i * d, t + k * d, d);
+            double pred;
+            if (i == 0)
+                pred = 0.0; /* a match may start in any column */
+            else
+                pred = fmin(fmin(cur[i - 1], prev[i]), prev[i - 1]);
+            cur[i] = kind == ORC_DTW ? c + pred : fmax(c, pred);
+        }
+        if (cur[m - 1] < best) {
+            best = cur[m - 1];
+            if (end)
+                *end = k;
+        }
+        double *tmp = prev;
+        prev = cur;
+        cur = tmp;
+    }
+    free(prev);
+    free(cur);
+    return best;
+}
+
+/* Sparse dog-keeper distance for subsequence search (Algorithm 3 with
+ * SUB = true): the column sweep of orc_sparse_dk without a band, where row 1
+ * joins the rows to visit in every column (a match may start anywhere) and
+ * the last row of every column is a candidate end.  Readings: d starts at
+ * +inf once, before the sweep (the listing resets it inside the column
+ * loop, which would keep only the last column's value, against the text's
+ * "each position as possible end"); a row-1 cell takes its own cost, like
+ * the whole-match start cell.  Returns the minimum when it is <= eps, +inf
+ * otherwise; *end as in orc_sub_distance; *cells counts evaluated cells. */
+double orc_sub_sparse_dk(const double *s, int64_t m, const double *t, int64_t n, int d,
+                         double eps, int64_t *end, int64_t *cells)
+{
+    if (end)
+        *end = -1;
+    if (cells)
+        *cells = 0;
+    if (m <= 0 || n <= 0)
+        return ORC_INF;
+    double *D = malloc(sizeof(double) * (size_t)(m + 2));
+    double *E = malloc(sizeof(double) * (size_t)(m + 2));
+    char *I = calloc((size_t)(m + 2), 1);
+    char *J = calloc((size_t)(m + 2), 1);
+    for (int64_t i = 0; i < m + 2; ++i)
+        D[i] = E[i] = ORC_INF;
+    I[1] = 1;
+    double best = ORC_INF;
+    int64_t evaluated = 0;
+    for (int64_t k = 1; k <= n; ++k) {
+        for (int64_t i = 1; i <= m; ++i) { /* I may grow upward while we sweep */
+            if (!I[i])
+                continue;
+            const double c = eucl(s + (i - 1) * d, t + (k - 1) * d, d);
+            ++evaluated;
+            if (c <= eps) {
+                const double pred = i == 1 ? 0.0 : fmin(fmin(D[i - 1], E[i]), E[i - 1]);
+                D[i] = fmax(c, pred);
+                if (i + 1 <= m)
+                    I[i + 1] = 1;
+                J[i] = 1;
+                if (i + 1 <= m)
+                    J[i + 1] = 1;
+            } else {
+                I[i] = 0;
+            }
+        }
+        if (D[m] < best) {
+            best = D[m];
+            if (end)
+                *end = k - 1;
+        }
+        for (int64_t i = 0; i < m + 2; ++i)
+            E[i] = D[i];
+        for (int64_t i = 0; i < m + 2; ++i)
+            D[i] = ORC_INF;
+        for (int64_t i = 0; i < m + 2; ++i) {
+            I[i] = J[i];
+            J[i] = 0;
+        }
+        I[1] = 1; /* SUB: every column may start a match */
+    }
+    free(D);
+    free(E);
+    free(I);
+    free(J);
+    if (cells)
+        *cells = evaluated;
+    if (!(best <= eps)) {
+        if (end)
+            *end = -1;
+        return ORC_INF;
+    }
+    return best;
+}
+
+/* Greedy dog-keeper for subsequence search (Algorithm 2): start at row 0 in
+ * the column of T closest to s_0 (the first such column), walk to the
+ * cheapest of (i+1, j), (i+1, j+1), (i, j+1) (the first in this order on
+ * ties; a column beyond T costs +inf) until the last row is reached, and
+ * return the largest cost met (early exit once it exceeds eps).  An upper
+ * bound of the subsequence DK: the walk is one admissible path.  *end: the
+ * column where the walk reached the last row. */
+double orc_sub_gdk(const double *s, int64_t m, const double *t, int64_t n, int d, double eps,
+                   int64_t *end)
+{
+    if (end)
+        *end = -1;
+    if (m <= 0 || n <= 0)
+        return ORC_INF;
+    int64_t i = 0, j = 0;
+    double g = ORC_INF;
+    for (int64_t k = 0; k < n; ++k) {
+        const double c = eucl(s, t + k * d, d);
+        if (c < g) {
+            g = c;
+            j = k;
+        }
+    }
+    if (g > eps)
+        return g;
+    while (i != m - 1) {
+        const double c_up = eucl(s + (i + 1) * d, t + j * d, d);
+        const double c_diag = j + 1 < n ? eucl(s + (i + 1) * d, t + (j + 1) * d, d) : ORC_INF;
+        const double c_right = j + 1 < n ? eucl(s + i * d, t + (j + 1) * d, d) : ORC_INF;
+        double c = c_up;
+        int64_t ni = i + 1, nj = j;
+        if (c_diag < c) {
+            c = c_diag;
+            ni = i + 1;
+            nj = j + 1;
+        }
+        if (c_right < c) {
+            c = c_right;
+            ni = i;
+            nj = j + 1;
+        }
+        i = ni;
+        j = nj;
+        g = fmax(g, c);
+        if (g > eps)
+            return g;
+    }
+    if (end)
+        *end = j;
+    return g;
+}
+
 /* DTW with early abandoning (Section 4, first paragraph): the minimum of a
  * row of the warping matrix bounds the final value from below, so stop as
  * soon as it exceeds eps.  Returns DTW when DTW <= eps, +inf otherwise. */

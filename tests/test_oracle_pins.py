@@ -415,3 +415,97 @@ def test_knn_ties_broken_by_id(orc):
     q = w.db[:32].copy()
     ids, dist = orc.knn(db, off, q, np.array([0, 32]), band=0.1, kind=0, k=3, method=True)
     assert list(ids[0]) == [0, 50, 51] and dist[0, 0] == 0.0 == dist[0, 2]
+
+
+# --- subsequence search (Algorithm 2; Algorithm 3 with SUB = true) ----------
+
+import oracle  # noqa: E402  (the same module the orc fixture provides)
+
+def _brute_sub(kind, s, t):
+    """min over every subsequence T[a..b] of the whole-match distance (no band),
+    and for each end b the best value over starts a."""
+    m, n = len(s), len(t)
+    per_end = []
+    for b in range(n):
+        best_b = math.inf
+        for a in range(b + 1):
+            seg = t[a:b + 1]
+            r = max(m, len(seg))
+            v = oracle.dtw(s, seg, r) if kind == 0 else oracle.dk(s, seg, r)
+            best_b = min(best_b, v)
+        per_end.append(best_b)
+    return min(per_end), per_end
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_subsequence_equals_min_over_all_subsequences(kind):
+    """The free-start/free-end DP equals the minimum, over every subsequence of
+    T, of the whole-match distance (itself pinned by path enumeration), and its
+    end column is an end at which that minimum is attained."""
+    rng = np.random.default_rng(7)
+    for trial in range(40):
+        d = int(rng.integers(1, 4))
+        m = int(rng.integers(1, 5))
+        n = int(rng.integers(1, 10))
+        s = rng.standard_normal((m, d))
+        t = rng.standard_normal((n, d))
+        v, end = oracle.sub_distance(kind, s, t)
+        bv, per_end = _brute_sub(kind, s, t)
+        assert math.isclose(v, bv, rel_tol=1e-12, abs_tol=1e-12), (trial, v, bv)
+        assert 0 <= end < n and math.isclose(per_end[end], bv, rel_tol=1e-12, abs_tol=1e-12)
+        # the smallest such end
+        assert all(per_end[b] > bv * (1 + 1e-12) + 1e-12 for b in range(end))
+
+
+def test_subsequence_sparse_dk_matches_plain_within_eps():
+    """Algorithm 3 with SUB = true visits only cells of cost <= eps: it returns
+    the subsequence DK when that is <= eps and +inf otherwise, never another
+    value, and visits fewer cells for a tighter eps."""
+    rng = np.random.default_rng(8)
+    for trial in range(60):
+        d = int(rng.integers(1, 4))
+        m = int(rng.integers(1, 7))
+        n = int(rng.integers(1, 30))
+        s = rng.standard_normal((m, d))
+        t = rng.standard_normal((n, d))
+        v, end = oracle.sub_distance(1, s, t)
+        last_cells = None
+        for f in (4.0, 2.0, 1.0 + 1e-9, 0.999, 0.5):
+            sv, send, cells = oracle.sub_sparse_dk(s, t, v * f)
+            if v <= v * f:
+                assert sv == pytest.approx(v, rel=1e-12) and send == end
+            else:
+                assert sv == math.inf and send == -1
+            if last_cells is not None:
+                assert cells <= last_cells
+            last_cells = cells
+        assert oracle.sub_sparse_dk(s, t, math.inf)[0] == pytest.approx(v, rel=1e-12)
+
+
+def test_subsequence_greedy_bounds_and_exact_copy():
+    """Algorithm 2 walks one admissible path, so it bounds the subsequence DK
+    from above; an exact copy of S inside T gives 0 for both, ending where the
+    copy ends."""
+    rng = np.random.default_rng(9)
+    for trial in range(60):
+        d = int(rng.integers(1, 4))
+        m = int(rng.integers(1, 7))
+        n = int(rng.integers(1, 30))
+        s = rng.standard_normal((m, d))
+        t = rng.standard_normal((n, d))
+        v, _ = oracle.sub_distance(1, s, t)
+        g, gend = oracle.sub_gdk(s, t)
+        assert g >= v - 1e-12
+        assert 0 <= gend < n
+        # early exit: a threshold below the bound returns a value above it
+        if g > 0:
+            ge, _ = oracle.sub_gdk(s, t, 0.5 * g)
+            assert ge > 0.5 * g
+    s = rng.standard_normal((5, 2))
+    t = rng.standard_normal((40, 2))
+    t[17:22] = s
+    for kind in (0, 1):
+        v, end = oracle.sub_distance(kind, s, t)
+        assert v == 0.0 and end == 21
+    g, gend = oracle.sub_gdk(s, t)
+    assert g == 0.0 and gend == 21
