@@ -285,6 +285,40 @@ KNN_API knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off, in
                                         int32_t distance, float *out, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Subsequence search (Section 4.1 Algorithm 2; Section 4.2 Algorithm 3     */
+/* with SUB = true): queries against every subsequence of one long series.  */
+
+/* For each query S (m points) the minimum over all subsequences T[a..b] of
+ * the long series T (n points, [n][d] point-major) of DTW(S, T[a..b]) (sum of
+ * squared costs, distance = KNN_DTW) or DK(S, T[a..b]) (max of Euclidean
+ * costs, KNN_DK), without a band: the free-start, free-end recursion in which
+ * every column may start a match and every column may end one.  out_dist
+ * [n_queries] receives the value, out_end [n_queries] the end b of the best
+ * subsequence (the smallest b on ties).  eps >= 0 (+inf: none): cells whose
+ * value exceeds eps (DTW units for DTW, Euclidean for DK) are dropped (values
+ * only grow along a path; for DK this is Algorithm 3's sparse visit); a
+ * result above eps is reported as +inf with end -1.  queries/q_offsets as in knn_scan; series, queries and
+ * outputs may be host or device memory.  Limits: 1 <= d <= 16; m <= 1024
+ * for d = 1, 512 for d = 2, 3, 256 for d = 4..8, 128 for d = 9..16 (else
+ * KNN_ERR_UNSUPPORTED); coordinates of magnitude well below 1e18 (sentinel
+ * points of that value pad T).  Synchronises `stream`. */
+KNN_API knn_status knn_subseq(const float *queries, const int64_t *q_offsets, int32_t n_queries,
+                              const float *series, int64_t n, int32_t d, int32_t distance,
+                              float eps, float *out_dist, int64_t *out_end, void *stream);
+
+/* Algorithm 2 (greedy dog-keeper for subsequence search): per query the
+ * largest Euclidean cost along the greedy walk that starts at row 0 in the
+ * column closest to s_0 (the first on ties) and moves to the cheapest of
+ * (i+1, j), (i+1, j+1), (i, j+1) until the last row; an upper bound of the
+ * subsequence DK.  out_ub [n_queries], out_end [n_queries] (the column where
+ * the walk reached the last row).  The walk stops early once the bound
+ * exceeds eps; it then reports that bound with end -1.  Arguments and memory
+ * as for knn_subseq; no limit on m. */
+KNN_API knn_status knn_subseq_greedy(const float *queries, const int64_t *q_offsets,
+                                     int32_t n_queries, const float *series, int64_t n, int32_t d,
+                                     float eps, float *out_ub, int64_t *out_end, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Learned proposal: a 1-D convolutional encoder (no counterpart in the     */
 /* paper; it generalises the upper-bound pre-pass of Section 4.3).  Three   */
 /* convolutions (kernel 5, 64 channels, ReLU), a mean over positions and a  */

@@ -38,7 +38,7 @@ STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA"
 EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
-           "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
+           "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_subseq", "knn_subseq_greedy", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
            "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach",
            "knn_encoder_params", "knn_encoder_loss_grad", "knn_encoder_save", "knn_encoder_load")
 
@@ -112,6 +112,10 @@ def lib() -> C.CDLL:
     L.knn_set_dp_shape.argtypes = [vp] + [C.c_int32] * 5
     L.knn_get_dp_shape.argtypes = [vp] + [C.c_int32] * 3 + [C.POINTER(C.c_int32)] * 2
     L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
+    L.knn_subseq.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, C.c_int32, C.c_int32, C.c_float,
+                             vp, vp, vp]
+    L.knn_subseq_greedy.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, C.c_int32, C.c_float, vp,
+                                    vp, vp]
     L.knn_set_lb_tile.argtypes = [vp] + [C.c_int32] * 4
     L.knn_get_lb_tile.argtypes = [vp, C.c_int32] + [C.POINTER(C.c_int32)] * 3
     L.knn_pairwise_noalloc.argtypes = [vp, vp, C.c_int64, vp, vp, C.c_int64, vp, vp, C.c_int64,
@@ -382,6 +386,33 @@ class Encoder:
             self.close()
         except Exception:
             pass
+
+
+def subseq(queries, q_offsets, series, *, distance: int = DK, eps: float = float("inf"),
+           greedy: bool = False, stream=None):
+    """Subsequence search of every query against one long series (Section 4.2,
+    Algorithm 3 with SUB = true; greedy=True: the Algorithm 2 upper bound).
+    queries [sum m][d], q_offsets [nq+1], series [n][d]: host or device.
+    Returns (values [nq] float32, ends [nq] int64) on the inputs' device."""
+    import torch
+    queries = _f32(queries)
+    q_offsets = _i64(q_offsets)
+    series = _f32(series)
+    nq = int(q_offsets.shape[0] - 1)
+    d = int(series.shape[1]) if series.ndim > 1 else 1
+    on_gpu = hasattr(series, "is_cuda") and series.is_cuda
+    dev = series.device if on_gpu else torch.device("cpu")
+    vals = torch.empty(nq, dtype=torch.float32, device=dev)
+    ends = torch.empty(nq, dtype=torch.int64, device=dev)
+    if greedy:
+        _check(lib().knn_subseq_greedy(_ptr(queries), _ptr(q_offsets), nq, _ptr(series),
+                                       int(series.shape[0]), d, eps, _ptr(vals), _ptr(ends),
+                                       _stream(stream)))
+    else:
+        _check(lib().knn_subseq(_ptr(queries), _ptr(q_offsets), nq, _ptr(series),
+                                int(series.shape[0]), d, distance, eps, _ptr(vals), _ptr(ends),
+                                _stream(stream)))
+    return vals, ends
 
 
 def dp_shapes(d: int) -> list[int]:
