@@ -470,6 +470,115 @@ def run_gpu(args):
     return 0
 
 
+SUB_METRIC = "exact subsequence search queries/sec and GCUPS (DTW & DK, free start and end)"
+
+
+def sub_cpu_baseline(w, n_sample: int) -> dict:
+    """The FP64 oracle's subsequence search on a sample of queries, one query
+    per thread (ctypes releases the GIL)."""
+    import concurrent.futures
+    import oracle
+    oracle.lib()
+    n_sample = min(n_sample, int(w.q_off.shape[0] - 1))
+    cores = min(os.cpu_count() or 1, n_sample)
+    t64 = w.t.astype(np.float64)
+    jobs = [(kind, w.q[w.q_off[i]:w.q_off[i + 1]].astype(np.float64))
+            for i in range(n_sample) for kind in (0, 1)]
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda j: oracle.sub_distance(j[0], j[1], t64), jobs))
+    dt = time.perf_counter() - t0
+    return {"value": len(jobs) / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_sample} queries x {w.t.shape[0]} points, DTW and DK, FP64 "
+                      f"free-start/free-end DP, {cores} threads", "seconds": dt}
+
+
+def run_subseq(args):
+    """Subsequence search workloads: every query against one long series."""
+    from synthdata import LONG_SERIES, make_long_series
+    cfg = dict(LONG_SERIES[args.workload])
+    if args.queries:
+        cfg["n_queries"] = args.queries
+    w = make_long_series(**cfg)
+    if args.impl == "reference":
+        steps = []
+        n_sample = args.cpu_sample or (os.cpu_count() or 1)
+        for _ in range(args.warmup + args.steps):
+            steps.append(sub_cpu_baseline(w, n_sample))
+        vals = [x["value"] for x in steps[args.warmup:]]
+        value = len(vals) / sum(1.0 / v for v in vals)
+        cb = dict(steps[-1])
+        cb["value"] = value
+        print(json.dumps({"impl": "reference", "metric": SUB_METRIC, "value": value,
+                          "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": args.workload, **cfg}, "cpu_baseline": cb,
+                          "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
+    import torch
+    import paper_1811_11076_gb300 as kw
+    kw.lib()
+    q, qo, t = (torch.from_numpy(x).cuda() for x in (w.q, w.q_off, w.t))
+    nq, m, n, d = int(qo.shape[0] - 1), int(cfg["q_length"]), int(w.t.shape[0]), w.d
+    for _ in range(max(args.warmup, 3)):
+        for kind in (kw.DTW, kw.DK):
+            kw.subseq(q, qo, t, distance=kind)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        ms = {kw.DTW: 0.0, kw.DK: 0.0}
+        for _ in range(args.steps):
+            for kind in (kw.DTW, kw.DK):
+                ev[0].record(stream)
+                kw.subseq(q, qo, t, distance=kind)
+                ev[1].record(stream)
+                ev[1].synchronize()
+                ms[kind] += ev[0].elapsed_time(ev[1])
+    total_ms = ms[kw.DTW] + ms[kw.DK]
+    value = 2 * nq * args.steps / (total_ms / 1000.0)
+    # rows per warp: 32 P >= m; every cell of the 32 P x (n + m - 1 rounded) sweep is
+    # computed, the algorithmic work counts the m x n cells at 2d+3 lane ops each
+    cells = nq * m * n
+    hbm_gbs, sm_max_mhz, peak_src = peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
+    achieved = cells * (2 * d + 3) * 2 * args.steps / (total_ms / 1000.0) / 1e12
+    clocks = clk.summary()
+    roof = {"kernel": "subseq_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
+            "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
+            "traffic": TRAFFIC.get(("subseq_kernel", args.workload)),
+            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz (max SM clock, "
+                           f"{peak_src})"}
+    # end to end from host buffers (series and queries copied in every call)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        for kind in (kw.DTW, kw.DK):
+            v, e = kw.subseq(w.q, w.q_off, w.t, distance=kind)
+    e2e_dt = time.perf_counter() - t0
+    line = {"metric": SUB_METRIC, "value": value, "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "queries": nq, "m": m,
+                       "band": "none (free start and end)",
+                       "l2": f"series {w.t.nbytes / 1e6:.0f} MB, streamed once per query"},
+            "per_distance": {("DTW" if k_ == kw.DTW else "DK"): {
+                "ms": ms[k_] / args.steps, "queries_per_s": nq * args.steps / (ms[k_] / 1000.0),
+                "gcups": cells * args.steps / (ms[k_] / 1000.0) / 1e9} for k_ in ms},
+            "roofline": roof, "clocks": clocks, "gpu_launches": 5 * 2 * args.steps,
+            "e2e": {"value": 2 * nq * e2e_steps / e2e_dt, "unit": "queries/s",
+                    "h2d_bytes_per_step": 2 * (w.q.nbytes + w.q_off.nbytes + w.t.nbytes),
+                    "d2h_bytes_per_step": 2 * nq * 12}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = sub_cpu_baseline(w, args.cpu_sample or (os.cpu_count() or 1))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,7 +591,8 @@ def main():
     ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=list(BENCH))
+    from synthdata import LONG_SERIES
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(BENCH) + list(LONG_SERIES))
     ap.add_argument("--queries", type=int, default=0,
                     help="queries per GPU (default: the workload's; smaller only for profiling)")
     ap.add_argument("--series", type=int, default=0,
@@ -494,6 +604,8 @@ def main():
     ap.add_argument("--lb-compaction", type=int, default=0, choices=[0, 1, 2],
                     help="LB_Box compaction: 0 automatic, 1 never, 2 always")
     args = ap.parse_args()
+    if args.workload in LONG_SERIES:
+        return run_subseq(args)
     select_workload(args.workload)
     if args.queries:
         globals()["N_QUERIES"] = args.queries

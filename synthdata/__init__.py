@@ -158,6 +158,63 @@ def make_workload(*, n_series: int, n_queries: int, d: int, length=64,
     )
 
 
+@dataclass
+class LongSeries:
+    """One long series and a batch of queries for subsequence search."""
+
+    d: int
+    t: np.ndarray             # [n, d] float32
+    q: np.ndarray             # [sum(qlen), d] float32
+    q_off: np.ndarray         # [Q+1] int64
+    meta: dict = field(default_factory=dict)
+
+
+def make_long_series(*, n: int, n_queries: int, d: int, q_length: int, n_classes: int = 20,
+                     seed: int = 0, noise_sigma: float = 0.1, batch: int = 4096) -> LongSeries:
+    """A long series made of consecutive class instances (the recipe of
+    make_workload, lengths U[q_length/2, 2 q_length]) and queries that are
+    fresh instances of length q_length (stand-in for querying one long ECG
+    recording)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lt = 2 * q_length
+    templ = _templates(rng, n_classes, lt, d, False)
+    chunks, total, last = [], 0, None
+    while total < n:
+        lens = rng.integers(q_length // 2, 2 * q_length + 1, size=batch)
+        classes = rng.integers(0, n_classes, size=batch).astype(np.int32)
+        knots = _warp_knots(rng, batch)
+        inst = [None] * batch
+        for L in np.unique(lens):
+            sel = np.nonzero(lens == L)[0]
+            nz = rng.standard_normal((len(sel), int(L), d)) * noise_sigma
+            block = _instances(templ, classes[sel], knots[sel], int(L), nz)
+            for j, i in enumerate(sel):
+                inst[i] = block[j]
+        chunk = np.concatenate(inst)
+        if last is not None:          # continue from where the previous chunk ended
+            chunk = chunk - chunk[0] + last
+        last = chunk[-1]
+        chunks.append(chunk.astype(np.float32))
+        total += chunk.shape[0]
+    pieces_all = np.concatenate(chunks)
+    t = pieces_all[:n].astype(np.float32)
+    qc = rng.integers(0, n_classes, size=n_queries).astype(np.int32)
+    qk = _warp_knots(rng, n_queries)
+    nz = rng.standard_normal((n_queries, q_length, d)) * noise_sigma
+    q = _instances(templ, qc, qk, q_length, nz).reshape(-1, d).astype(np.float32)
+    q_off = np.arange(n_queries + 1, dtype=np.int64) * q_length
+    return LongSeries(d=d, t=t, q=q, q_off=q_off,
+                      meta=dict(seed=seed, n_classes=n_classes, q_length=q_length))
+
+
+LONG_SERIES = {
+    # one series of 1,000,000 points, d=1, 1,024 queries of 256 points
+    "subseq_d1_T1M_m256": dict(n=1_000_000, n_queries=1024, d=1, q_length=256, seed=5),
+    # d=3, 1,000,000 points, 1,024 queries of 128 points
+    "subseq_d3_T1M_m128": dict(n=1_000_000, n_queries=1024, d=3, q_length=128, seed=6),
+}
+
+
 # Named workloads (sizes of the scan's benchmark configurations).
 WORKLOADS = {
     # d=2, 1,000 series of length 64, 10 queries, 5 classes, seed 0
