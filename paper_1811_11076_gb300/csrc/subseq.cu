@@ -10,19 +10,18 @@
 //
 // Work mapping: one warp per query, a systolic array.  Lane L keeps P query
 // rows in registers (rows L*P + e - off, e < P, off = 32P - m, so the last
-// row sits at lane 31, slot P-1); the rows below row 0 are virtual, with cost
-// weight 0 and value 0, which gives row 0 its zero predecessor (the free
-// start).  Step t computes anti-diagonal t: cell e of a lane is (i, t - i), so
+// row sits at lane 31, slot P-1); the rows below row 0 are virtual, held at
+// value 0, which gives row 0 its zero predecessor (the free start).  Step t computes anti-diagonal t: cell e of a lane is (i, t - i), so
 // the P cells are independent; a cell needs its own row and the row below at
 // step t-1 and the row below at step t-2 (one shuffle each at the lane edge).
 // The series streams through: each step a lane loads the one column it sees
 // first, held with the others it needs in a ring of P points.  T is copied
 // with sentinel points (1e18) on both sides, so cells before the start or
 // after the end cost about 1e36 per coordinate and never win.  Cells whose
-// value exceeds the caller's threshold are dropped (+inf): values only grow
-// along a path, so such a cell cannot lead to a result within it (for DK this
-// is Algorithm 3's sparse visit of the cells of cost <= eps); a result above
-// the threshold is therefore reported as +inf.
+// value exceeds the caller's threshold are capped just above it: values only
+// grow along a path, so such a cell cannot lead to a result within it (for DK
+// this is Algorithm 3's sparse visit of the cells of cost <= eps); a result
+// above the threshold is reported as +inf.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -65,11 +64,16 @@ __global__ void __launch_bounds__(SUB_THREADS) subseq_kernel(const SubArgs a)
     const int base = lane * P - off;  // row of slot 0
     const float *qp = a.q + a.q_off[qi];
 
-    float qv[P][D], w[P], cur[P], prv[P];
+    // cap: a cell's value is min(value, cap).  Virtual rows: 0 (values are
+    // >= 0, so they stay 0).  Real rows: the float just above the threshold,
+    // so a cell above it stays above it, and so does every path through it
+    // (values only grow along a path), while values within it are unchanged.
+    float qv[P][D], cap[P], cur[P], prv[P];
+    const float capv = a.eps2 < KNN_INF ? nextafterf(a.eps2, KNN_INF) : KNN_INF;
 #pragma unroll
     for (int e = 0; e < P; ++e) {
         const int i = base + e;
-        w[e] = i >= 0 ? 1.f : 0.f;
+        cap[e] = i >= 0 ? capv : 0.f;
         load_point<D>(qp + (int64_t)(i >= 0 ? i : 0) * D, qv[e]);
         cur[e] = prv[e] = i >= 0 ? KNN_INF : 0.f;
     }
@@ -101,9 +105,8 @@ __global__ void __launch_bounds__(SUB_THREADS) subseq_kernel(const SubArgs a)
                 const float up = e > 0 ? cur[e - 1] : up1;
                 const float dg = e > 0 ? prv[e - 1] : up2;
                 const float mn = fmin3(left, up, dg);
-                const float c = sqdist_acc<D>(qv[e], xw[(u - e + P) % P], 0.f) * w[e];
-                float v = KIND == 0 ? c + mn : fmaxf(c, mn);
-                v = v > a.eps2 ? KNN_INF : v;
+                const float c = sqdist_acc<D>(qv[e], xw[(u - e + P) % P], 0.f);
+                const float v = fminf(KIND == 0 ? c + mn : fmaxf(c, mn), cap[e]);
                 prv[e] = cur[e];
                 cur[e] = v;
             }
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(SUB_THREADS) subseq_kernel(const SubArgs a)
         }
     }
     if (lane == 31) {
-        const bool found = best < 1e30f;
+        const bool found = best <= a.eps2 && best < 1e30f;
         a.out[qi] = found ? (KIND == 0 ? best : sqrtf(best)) : KNN_INF;
         a.out_end[qi] = found ? best_k : -1;
     }
