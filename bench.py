@@ -62,8 +62,8 @@ TRAIN_PAIRS = 200_000
 # captures of the current kernels (the summaries in profiles/ give the commands).
 # A kernel changed since its capture has no entry (traffic null).
 TRAFFIC = {
-    # mean of the DTW and DK launches of one scan (profiles/dram_traffic_*.md,
-    # profiles/subseq_kernel_*.md)
+    # mean of the DTW and DK launches of one scan, one-pass DRAM counters of
+    # the full workload
     ("lb_compact_kernel", "scale_d3_n100k_L256"): 6.73e9,
     ("dp_kernel", "scale_d3_n100k_L256"): 2.49e9,
     ("subseq_kernel", "subseq_d1_T1M_m256"): 5.78e6,
