@@ -216,6 +216,7 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
     import paper_1811_11076_gb300 as kw
+    from paper_1811_11076_gb300.shard import max_over_ranks, query_shard
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -227,9 +228,8 @@ def run_gpu(args):
 
     w = workload(world)
     nq = N_QUERIES
-    q0, q1 = w.q_off[rank * N_QUERIES], w.q_off[rank * N_QUERIES + nq]
+    (q0, q1), q_off = query_shard(w.q_off, rank, world, nq)
     q_host = np.ascontiguousarray(w.q[q0:q1])
-    q_off = w.q_off[rank * N_QUERIES:rank * N_QUERIES + nq + 1] - q0
     db_dev = torch.from_numpy(w.db).cuda()
     kinds = {"both": (kw.DTW, kw.DK), "dtw": (kw.DTW,), "dk": (kw.DK,)}[args.only]
     seed_mode = {"greedy": kw.SEED_GREEDY, "lb": kw.SEED_LB, "none": kw.SEED_NONE,
@@ -296,11 +296,7 @@ def run_gpu(args):
             step(collected)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
     total_queries = nq * len(kinds) * args.steps * world
     value = total_queries / (ms / 1000.0)
 
@@ -400,11 +396,7 @@ def run_gpu(args):
             dbs[kind].scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
                            out=(ids_h, dst_h, cnt_h))
     barrier()
-    e2e_dt = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, device="cuda")
     h2d = (q_host.nbytes + q_off.nbytes) * len(kinds)
     d2h = (ids_h.numel() * 8 + dst_h.numel() * 4 + cnt_h.numel() * 8) * len(kinds)
     e2e = {"value": nq * len(kinds) * e2e_steps * world / e2e_dt, "unit": "queries/s",
