@@ -468,6 +468,95 @@ def run_gpu(args):
     return 0
 
 
+def tightness_table(kw, dims, lengths, n_pairs: int, band: float, data: str, seed: int = 0):
+    """Mean LB_Box / DTW over random pairs for every (d, n) (Section 3's
+    Theorem: the ratio falls as d grows).  data "iid": elements U[0, 1]
+    (the Theorem's setting); "classes": random pairs of the class-structured
+    synthetic series.  LB_Box(T, env(S)) and DTW(S, T) on the GPU."""
+    import torch
+    from synthdata import make_workload
+    rng = np.random.default_rng(seed)
+    rows = []
+    for d in dims:
+        for n in lengths:
+            if data == "iid":
+                S = rng.random((n_pairs, n, d), dtype=np.float32)
+                T = rng.random((n_pairs, n, d), dtype=np.float32)
+            else:
+                w = make_workload(n_series=2 * n_pairs, n_queries=1, d=d, length=n, n_classes=10,
+                                  seed=seed + d * 1000 + n)
+                X = w.db.reshape(2 * n_pairs, n, d)
+                S, T = X[:n_pairs], X[n_pairs:]
+            off = np.arange(n_pairs + 1, dtype=np.int64) * n
+            db = kw.KnnDB(torch.from_numpy(T.reshape(-1, d)).cuda(), off)
+            lb = np.empty(n_pairs)
+            for i in range(n_pairs):
+                lb[i] = float(db.lb_box(torch.from_numpy(S[i]).cuda(), band, 0)[i])
+            db.close()
+            pa = torch.arange(n_pairs, dtype=torch.int64, device="cuda")
+            dtw, _ = kw.pairwise(torch.from_numpy(S.reshape(-1, d)).cuda(),
+                                 torch.from_numpy(off).cuda(),
+                                 torch.from_numpy(T.reshape(-1, d)).cuda(),
+                                 torch.from_numpy(off).cuda(), pa, pa, band=band, distance=kw.DTW)
+            dtw = dtw.cpu().numpy().astype(np.float64)
+            ok = dtw > 0
+            rows.append({"d": d, "n": n, "mean_ratio": float(np.mean(lb[ok] / dtw[ok])),
+                         "ratio_of_means": float(lb.mean() / dtw.mean()), "pairs": int(ok.sum())})
+    return rows
+
+
+def accuracy_table(kw, dims, lengths, n_series: int, n_queries: int, band: float,
+                   seed: int = 0, noise: float = 0.1, n_classes: int = 10):
+    """1-NN classification accuracy of DTW and DK (the exact scan with k = 1) on
+    the class-structured synthetic data (instance noise N(0, noise^2)), for
+    every (d, n)."""
+    import torch
+    from synthdata import make_workload
+    rows = []
+    for d in dims:
+        for n in lengths:
+            w = make_workload(n_series=n_series, n_queries=n_queries, d=d, length=n,
+                              n_classes=n_classes, seed=seed + d * 1000 + n, noise_sigma=noise)
+            db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
+            row = {"d": d, "n": n}
+            for kind, name in ((kw.DTW, "dtw"), (kw.DK, "dk")):
+                ids, _ = db.scan(torch.from_numpy(w.q).cuda(), w.q_off, k=1, band=band,
+                                 distance=kind, seed=kw.SEED_LB)
+                ids = ids.cpu().numpy()[:, 0]
+                row["acc_" + name] = float(np.mean(w.db_labels[ids] == w.q_labels))
+                row["ids_" + name] = ids.tolist() if n_queries <= 64 else None
+            db.close()
+            rows.append(row)
+    return rows
+
+
+def run_experiment(args):
+    """Tightness sweep (the Theorem's trend) or 1-NN accuracy, one JSON line."""
+    import paper_1811_11076_gb300 as kw
+    kw.lib()
+    t0 = time.perf_counter()
+    if args.experiment == "tightness":
+        rows = {data: tightness_table(kw, (1, 2, 4, 8, 16),
+                                      (32, 64, 128, 256, 512), 128, 0.1, data)
+                for data in ("iid", "classes")}
+        line = {"experiment": "tightness", "quantity": "LB_Box / DTW, band 10 %",
+                "pairs_per_cell": 128, "rows": rows}
+    else:
+        rows = {}
+        for noise in (1.0, 3.0):
+            rows[f"noise {noise}"] = accuracy_table(kw, (1, 2, 4, 8, 16), (64, 128, 256), 5000,
+                                                    400, 0.1, noise=noise, n_classes=50)
+            for r in rows[f"noise {noise}"]:
+                r.pop("ids_dtw", None)
+                r.pop("ids_dk", None)
+        line = {"experiment": "accuracy",
+                "quantity": "1-NN accuracy, 50 classes of warped random walks, band 10 %",
+                "series": 5000, "queries": 400, "rows": rows}
+    line["seconds"] = time.perf_counter() - t0
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 SUB_METRIC = "exact subsequence search queries/sec and GCUPS (DTW & DK, free start and end)"
 
 
@@ -599,9 +688,14 @@ def main():
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default="", help="P,G: fix the DP shape instead of tuning it")
+    ap.add_argument("--experiment", default="", choices=["", "tightness", "accuracy"],
+                    help="instead of the throughput line: the LB_Box tightness sweep or the "
+                         "1-NN accuracy of DTW and DK")
     ap.add_argument("--lb-compaction", type=int, default=0, choices=[0, 1, 2],
                     help="LB_Box compaction: 0 automatic, 1 never, 2 always")
     args = ap.parse_args()
+    if args.experiment:
+        return run_experiment(args)
     if args.workload in LONG_SERIES:
         return run_subseq(args)
     select_workload(args.workload)
