@@ -543,7 +543,7 @@ def run_experiment(args):
                 "pairs_per_cell": 128, "rows": rows}
     else:
         rows = {}
-        for noise in (1.0, 3.0):
+        for noise in (3.0, 6.0):
             rows[f"noise {noise}"] = accuracy_table(kw, (1, 2, 4, 8, 16), (64, 128, 256), 5000,
                                                     400, 0.1, noise=noise, n_classes=50)
             for r in rows[f"noise {noise}"]:
