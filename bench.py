@@ -271,8 +271,8 @@ def run_gpu(args):
     r = int(np.float64(np.float32(BAND)) * LENGTH)
     graph = BENCH[WORKLOAD]["graph"] and not args.no_graph
     for kind in kinds:
-        if args.lb_compaction:
-            dbs[kind].set_lb_tile(kind, 0, 0, args.lb_compaction)
+        if args.lb_compaction or args.lb_qtile:
+            dbs[kind].set_lb_tile(kind, args.lb_qtile, 0, args.lb_compaction)
         if args.shape:
             P, G = (int(v) for v in args.shape.split(","))
             dbs[kind].set_dp_shape(kind, r, LENGTH, P, G)
@@ -691,6 +691,8 @@ def main():
     ap.add_argument("--experiment", default="", choices=["", "tightness", "accuracy"],
                     help="instead of the throughput line: the LB_Box tightness sweep or the "
                          "1-NN accuracy of DTW and DK")
+    ap.add_argument("--lb-qtile", type=int, default=0, choices=[0, 4, 8, 16],
+                    help="queries per LB_Box pass (0: 16, or tuned)")
     ap.add_argument("--lb-compaction", type=int, default=0, choices=[0, 1, 2],
                     help="LB_Box compaction: 0 automatic, 1 never, 2 always")
     args = ap.parse_args()
