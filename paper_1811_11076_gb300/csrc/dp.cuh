@@ -59,15 +59,66 @@ __device__ __forceinline__ void load_point_prefix(const float *p, int idx, int l
     load_point<D>(p + clampi(idx, -1, last) * D, v);
 }
 
-template <int D, int P, int KIND>
+// Rows of the shared-memory window of one lane group (WIN kernels): the
+// newest row any lane reads and the G-1 strides of P below it, plus one, as
+// a power of two.
+__host__ __device__ constexpr int dp_win_rows(int G, int P)
+{
+    int w = 1;
+    while (w < (G - 1) * P + 2)
+        w <<= 1;
+    return w;
+}
+// Slot of row r (any integer, taken modulo W) in a window: rows P apart sit in
+// adjacent slots, so the G lanes of a group, which read rows P apart, hit
+// consecutive slots, and with a row stride of an odd number of 16-byte units
+// eight such float4 reads fall in distinct bank quads.
+template <int P>
+__device__ __forceinline__ int dp_win_slot(int r, int wp_mask)
+{
+    constexpr int LP = (P == 1) ? 0 : (P == 2) ? 1 : (P == 4) ? 2 : (P == 8) ? 3 : 4;
+    static_assert((1 << LP) == P, "window path needs P a power of two");
+    return (r & (P - 1)) * (wp_mask + 1) + ((r >> LP) & wp_mask);
+}
+// WIN kernels: the group's newest query row (s - h_0) and series column
+// (s + h_{G-1} + P) of step s come in 2*(D/4) float4 pieces, one per lane
+// lam < 2*(D/4) (G >= 8 and D <= 16, so a group has lanes enough).
+template <int D>
+__device__ __forceinline__ float4 dp_win_fetch(const float *qp, const float *xp, int m, int n,
+                                               int lam, int h0, int hT, int P, int s)
+{
+    constexpr int C = D / 4;
+    const bool isx = lam >= C;
+    const int c = isx ? lam - C : lam;
+    const float *src = isx ? xp + (int64_t)clampi(s + hT + P, -1, n - 1) * D
+                           : qp + (int64_t)clampi(s - h0, -1, m - 1) * D;
+    return __ldg(reinterpret_cast<const float4 *>(src) + c);
+}
+// Dynamic shared memory of a WIN kernel CTA: 32P rows per array per warp.
+__host__ __device__ constexpr size_t dp_win_bytes(int D, int P)
+{
+    return (size_t)(DP_THREADS / 32) * 2 * 32 * P * (D + 4) * sizeof(float);
+}
+
+template <int D, int P, int KIND, bool WIN>
 __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
 {
     constexpr int U = P + 1;
+    constexpr int RS = D + 4;  // window row stride in floats (16-byte aligned)
     const int lane = threadIdx.x & 31;
     const int G = a.G;
     const int lam = lane & (G - 1);
     const int gbase = lane & ~(G - 1);
     const unsigned lt_mask = (1u << gbase) - 1u;
+    // WIN: the group's windows of the last W query rows and series columns
+    extern __shared__ __align__(16) float dwin[];
+    const int W = WIN ? dp_win_rows(G, P) : P;
+    const int wp_mask = W / P - 1;
+    float *qwin = dwin + (size_t)(((threadIdx.x >> 5) * (32 / G) + (lane / G)) * 2 * W) * RS;
+    float *xwin = qwin + (size_t)W * RS;
+    // WIN: the pieces of the next two steps, loaded two steps ahead
+    float4 pf0 = make_float4(0.f, 0.f, 0.f, 0.f), pf1 = pf0;
+    const bool win_loader = WIN && lam < 2 * (D / 4);
 
     float qw[U][D], xw[U][D];
     float E[P], O[P], mE[P], mO[P];
@@ -169,6 +220,27 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                             load_point_prefix<D>(qp, s0 - h - ((U - p) % U), m - 1, qw[p]);
                             load_point_prefix<D>(xp, s0 + h + p, n - 1, xw[p]);
                         }
+                        if constexpr (WIN) {
+                            // the (G-1)P rows and columns before the first step's
+                            // newest, in float4 pieces spread over the group
+                            const int h0 = lo / 2, hT = lo / 2 + P * (G - 1);
+                            const int nf = (G - 1) * P * (D / 4);
+                            for (int t = lam; t < nf; t += G) {
+                                const int k = t / (D / 4), c = t - k * (D / 4);
+                                const int rq = s0 - h0 - (G - 1) * P + k;
+                                const int cx = s0 + h0 + P + k;
+                                const float4 vq = __ldg(reinterpret_cast<const float4 *>(
+                                    qp + (int64_t)clampi(rq, -1, m - 1) * D) + c);
+                                const float4 vx = __ldg(reinterpret_cast<const float4 *>(
+                                    xp + (int64_t)clampi(cx, -1, n - 1) * D) + c);
+                                reinterpret_cast<float4 *>(qwin + dp_win_slot<P>(rq, wp_mask) * RS)[c] = vq;
+                                reinterpret_cast<float4 *>(xwin + dp_win_slot<P>(cx, wp_mask) * RS)[c] = vx;
+                            }
+                            if (win_loader) {
+                                pf0 = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s0);
+                                pf1 = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s0 + 1);
+                            }
+                        }
                         active = true;
                         st_calls += (lam == 0);
                     }
@@ -183,8 +255,36 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int s = s0 + u;
-            load_point_prefix<D>(qp, s - h, m - 1, qw[u]);
-            load_point_prefix<D>(xp, s + h + P, n - 1, xw[(u + P) % U]);
+            if constexpr (WIN) {
+                // the group brings this step's newest row and column into its
+                // windows with coalesced loads; each lane then reads its own
+                // from shared memory instead of scattered global lines
+                const int h0 = h - P * lam, hT = h0 + P * (G - 1);
+                if (win_loader) {
+                    const bool isx = lam >= D / 4;
+                    const int c = isx ? lam - D / 4 : lam;
+                    float *dst = isx ? xwin + dp_win_slot<P>(s + hT + P, wp_mask) * RS
+                                     : qwin + dp_win_slot<P>(s - h0, wp_mask) * RS;
+                    reinterpret_cast<float4 *>(dst)[c] = pf0;
+                    pf0 = pf1;
+                    pf1 = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s + 2);
+                }
+                __syncwarp();
+                const float4 *qs =
+                    reinterpret_cast<const float4 *>(qwin + dp_win_slot<P>(s - h, wp_mask) * RS);
+                const float4 *xs =
+                    reinterpret_cast<const float4 *>(xwin + dp_win_slot<P>(s + h + P, wp_mask) * RS);
+#pragma unroll
+                for (int c = 0; c < D / 4; ++c) {
+                    const float4 vq = qs[c], vx = xs[c];
+                    qw[u][4 * c] = vq.x; qw[u][4 * c + 1] = vq.y; qw[u][4 * c + 2] = vq.z; qw[u][4 * c + 3] = vq.w;
+                    float *xd = xw[(u + P) % U];
+                    xd[4 * c] = vx.x; xd[4 * c + 1] = vx.y; xd[4 * c + 2] = vx.z; xd[4 * c + 3] = vx.w;
+                }
+            } else {
+                load_point_prefix<D>(qp, s - h, m - 1, qw[u]);
+                load_point_prefix<D>(xp, s + h + P, n - 1, xw[(u + P) % U]);
+            }
 
             float up = __shfl_up_sync(KNN_FULL_MASK, O[P - 1], 1, G);
             up = (lam == 0) ? KNN_INF : up;
@@ -286,13 +386,45 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
     }
 }
 
+// The shared-memory window pays where a point is wide (d >= 8) and a group
+// has enough lanes to load it cooperatively (G >= 8).
+template <int D, int P>
+constexpr bool dp_has_win()
+{
+    return D >= 8 && D <= 16 && D % 4 == 0 && (P & (P - 1)) == 0 && P >= 2 && P <= 16;
+}
+
 template <int D, int P>
 bool dp_launch_tpl(const DpArgs &a, int kind, int grid, cudaStream_t st)
 {
+    if constexpr (dp_has_win<D, P>()) {
+        if (a.G >= 8) {
+            const size_t smem = dp_win_bytes(D, P);
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(dp_kernel<D, P, 0, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaFuncSetAttribute(dp_kernel<D, P, 1, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                cudaFuncSetAttribute(dp_kernel<D, P, 0, true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+                cudaFuncSetAttribute(dp_kernel<D, P, 1, true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+                attr = true;
+            }
+            if (kind == 0)
+                dp_kernel<D, P, 0, true><<<grid, DP_THREADS, smem, st>>>(a);
+            else
+                dp_kernel<D, P, 1, true><<<grid, DP_THREADS, smem, st>>>(a);
+            return true;
+        }
+    }
     if (kind == 0)
-        dp_kernel<D, P, 0><<<grid, DP_THREADS, 0, st>>>(a);
+        dp_kernel<D, P, 0, false><<<grid, DP_THREADS, 0, st>>>(a);
     else
-        dp_kernel<D, P, 1><<<grid, DP_THREADS, 0, st>>>(a);
+        dp_kernel<D, P, 1, false><<<grid, DP_THREADS, 0, st>>>(a);
     return true;
 }
 
@@ -301,9 +433,11 @@ int dp_occupancy_tpl(int kind)
 {
     int blocks = 0;
     if (kind == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dp_kernel<D, P, 0>, DP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dp_kernel<D, P, 0, false>,
+                                                      DP_THREADS, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dp_kernel<D, P, 1>, DP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, dp_kernel<D, P, 1, false>,
+                                                      DP_THREADS, 0);
     return blocks;
 }
 

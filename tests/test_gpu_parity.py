@@ -351,6 +351,33 @@ def test_every_dp_shape_gives_identical_results(kw, kind):
 
 
 @pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d", [8, 16])
+@pytest.mark.parametrize("band", [0.1, 0.3])
+def test_wide_point_dp_shapes(kw, kind, d, band):
+    """d >= 8 with 8 or more lanes per pair stages query rows and series
+    columns in shared memory: every such shape returns the oracle's result."""
+    w = make_workload(n_series=600, n_queries=4, d=d, length=160, n_classes=6, seed=50 + d,
+                      correlated=True)
+    k = 4
+    r = oracle.band_radius(160, 160, f32(band))
+    oids, odist = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(band), kind=kind, k=k)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    shapes = []
+    for P in kw.dp_shapes(d):
+        G = 1
+        while G * P < r + 1:
+            G *= 2
+        shapes += [(P, g) for g in (G, 2 * G) if 8 <= g <= 32]
+    assert {g for _, g in shapes} >= ({8, 16, 32} if band == 0.1 else {32})
+    for seed in (kw.SEED_NONE, kw.SEED_LB):
+        for P, G in shapes:
+            db.set_dp_shape(kind, r, 160, P, G)
+            ids, dist = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kind, seed=seed)
+            check_knn(ids.cpu().numpy(), dist.cpu().numpy(), oids, odist, kind, k)
+    db.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("d,lengths,nq", [(3, (40, 300), 21), (16, (300, 700), 9)])
 def test_lb_tiles_and_windows_give_identical_results(kw, kind, d, lengths, nq):
     """LB_Box with 4, 8 or 16 queries per pass, whole envelopes or windows of
