@@ -311,7 +311,8 @@ def test_invalid_arguments(kw):
     db.close()
 
 
-def test_scan_simple_north_star_form(kw):
+def test_scan_simple_single_query_form(kw):
+    """knn_scan_simple: one host query against host series given by lengths."""
     w = make_workload(n_series=400, n_queries=1, d=3, length=40, n_classes=4, seed=14)
     lens = w.db_lengths()
     for kind in (0, 1):
