@@ -417,6 +417,35 @@ def test_knn_ties_broken_by_id(orc):
     assert list(ids[0]) == [0, 50, 51] and dist[0, 0] == 0.0 == dist[0, 2]
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("band", [0.2, 0.5, 1.0])
+def test_pairwise_matches_path_enumeration(orc, kind, band):
+    """The pair list form (knn_pairwise's oracle): each listed pair of two
+    different sets of uneven series against brute force over all warping
+    paths, including pairs whose end cell lies outside the band (+inf)."""
+    rng = np.random.default_rng(int(band * 10) + 7 * kind)
+    la, lb_ = [1, 3, 4, 6, 5], [2, 6, 1, 5]
+    a = [rand_series(rng, n, 2) for n in la]
+    b = [rand_series(rng, n, 2) for n in lb_]
+    a_off = np.concatenate([[0], np.cumsum(la)]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum(lb_)]).astype(np.int64)
+    pairs = [(i, j) for i in range(len(a)) for j in range(len(b))]
+    order = rng.permutation(len(pairs))
+    pa = np.array([pairs[o][0] for o in order] + [2, 2])
+    pb = np.array([pairs[o][1] for o in order] + [1, 1])
+    bf = float(np.float32(band))
+    got = orc.pairwise(np.concatenate(a), a_off, np.concatenate(b), b_off, pa, pb, band=bf,
+                       kind=kind)
+    brute = brute_dtw if kind == 0 else brute_dk
+    n_inf = 0
+    for x, (i, j) in enumerate(zip(pa, pb)):
+        r = orc.band_radius(la[i], lb_[j], bf)
+        exp = brute(a[i], b[j], r)
+        n_inf += exp == INF
+        assert got[x] == pytest.approx(exp, rel=1e-12, abs=1e-12), (i, j, r)
+    assert (n_inf > 0) == (band < 1.0)
+
+
 # --- subsequence search (Algorithm 2; Algorithm 3 with SUB = true) ----------
 
 import oracle  # noqa: E402  (the same module the orc fixture provides)
