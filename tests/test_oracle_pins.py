@@ -223,17 +223,21 @@ def test_lb_box_brute_small(orc):
     rng = np.random.default_rng(8)
     s, t = rand_series(rng, 6, 2), rand_series(rng, 6, 2)
     r = 1
-    total = 0.0
+    per_point = []
     for i in range(6):
         w = t[max(0, i - r): i + r + 1]
         lo, hi = w.min(axis=0), w.max(axis=0)
         gx = np.linspace(lo[0], hi[0], 401)
         gy = np.linspace(lo[1], hi[1], 401)
         X, Y = np.meshgrid(gx, gy)
-        total += float(np.min((X - s[i, 0]) ** 2 + (Y - s[i, 1]) ** 2))
+        per_point.append(float(np.min((X - s[i, 0]) ** 2 + (Y - s[i, 1]) ** 2)))
+    total, worst = sum(per_point), max(per_point)
     # the grid minimum can only overshoot the true minimum, by O(spacing^2)
     lb = orc.lb_box(s, t, r)
     assert lb <= total + 1e-12 and total - lb < 1e-4 * (1.0 + total)
+    # the max form: the largest per-point box distance (the DK^2 bound)
+    lbm = orc.lb_box(s, t, r, form=1)
+    assert lbm <= worst + 1e-12 and worst - lbm < 1e-4 * (1.0 + worst)
 
 
 # ---------------------------------------------------------------------------
@@ -252,11 +256,13 @@ def test_gdk_is_an_upper_bound_and_a_path_value(orc):
             assert g == INF
             continue
         assert g >= dk - 1e-12 and gs >= dtw - 1e-12
-        # the greedy value is the value of one admissible path
+        # both greedy values belong to ONE admissible path: its max of Euclidean
+        # costs is GDK and its sum of squared costs is the DTW greedy bound
         paths = all_paths(m, n, r)
-        maxes = {round(max(math.sqrt(float(np.sum((s[i] - t[j]) ** 2))) for i, j in p), 10)
+        pairs = {(round(max(math.sqrt(float(np.sum((s[i] - t[j]) ** 2))) for i, j in p), 10),
+                  round(sum(float(np.sum((s[i] - t[j]) ** 2)) for i, j in p), 10))
                  for p in paths}
-        assert round(g, 10) in maxes
+        assert (round(g, 10), round(gs, 10)) in pairs
 
 
 def test_gdk_zero_band_equals_dk(orc):
@@ -349,6 +355,12 @@ def test_hand_computed_examples(orc):
         if "lb_box" in c:
             assert orc.lb_box(s, t, c["r"]) == pytest.approx(c["lb_box"], rel=1e-12,
                                                              abs=1e-12), c["name"]
+        if "lb_box_max" in c:
+            assert orc.lb_box(s, t, c["r"], form=1) == pytest.approx(
+                c["lb_box_max"], rel=1e-12, abs=1e-12), c["name"]
+        if "greedy_dtw" in c:
+            assert orc.greedy_dtw(s, t, c["r"]) == pytest.approx(
+                c["greedy_dtw"], rel=1e-12), c["name"]
 
 
 # ---------------------------------------------------------------------------
