@@ -22,6 +22,8 @@ with shape ``[len_i, d]``, float32.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+import os
+from concurrent.futures import ThreadPoolExecutor
 from typing import Optional
 
 import numpy as np
@@ -83,76 +85,115 @@ def _warp_knots(rng: np.random.Generator, count: int) -> np.ndarray:
     return cum / cum[:, -1:]
 
 
-def _instances(templates: np.ndarray, classes: np.ndarray, knots: np.ndarray,
-               length: int, noise: np.ndarray) -> np.ndarray:
-    """Resample templates[classes] at warped positions; returns [B, length, d]."""
-    B = classes.shape[0]
-    lt = templates.shape[1]
-    u = np.linspace(0.0, 1.0, length) if length > 1 else np.zeros(1)
+def _resample(templ_flat: np.ndarray, lt: int, classes: np.ndarray, knots: np.ndarray,
+              lens: np.ndarray, noise: np.ndarray) -> np.ndarray:
+    """Instances of the templates of ``classes`` (series i has lens[i] points):
+    point p of series i takes the template at the warped position of
+    u = p / (lens[i] - 1), linearly interpolated, plus its noise.
+    templ_flat is [n_classes * lt, d] float32; noise is [sum(lens), d] float32
+    and is overwritten with the result, which is returned."""
+    lens = np.asarray(lens, dtype=np.int64)
+    sid = np.repeat(np.arange(lens.shape[0]), lens)                    # series of each point
+    start = np.zeros(lens.shape[0], dtype=np.int64)
+    np.cumsum(lens[:-1], out=start[1:])
+    p = np.arange(sid.shape[0], dtype=np.int64) - start[sid]
+    u = p / np.maximum(lens[sid] - 1, 1)
     # piecewise-linear warp: knot x positions are uniform in [0,1]
     seg = np.minimum((u * N_WARP_SEGMENTS).astype(np.int64), N_WARP_SEGMENTS - 1)
     frac = u * N_WARP_SEGMENTS - seg
-    w = knots[:, seg] * (1.0 - frac) + knots[:, seg + 1] * frac       # [B, length]
+    w = knots[sid, seg] * (1.0 - frac) + knots[sid, seg + 1] * frac
     tau = np.clip(w, 0.0, 1.0) * (lt - 1)
     i0 = np.minimum(np.floor(tau).astype(np.int64), lt - 2 if lt > 1 else 0)
-    f = (tau - i0)[..., None]
-    t = templates[classes]                                            # [B, lt, d]
-    g0 = np.take_along_axis(t, i0[..., None], axis=1)
-    g1 = np.take_along_axis(t, np.minimum(i0 + 1, lt - 1)[..., None], axis=1)
-    return g0 * (1.0 - f) + g1 * f + noise
+    f = (tau - i0).astype(np.float32)[:, None]
+    base = classes.astype(np.int64)[sid] * lt
+    g0 = templ_flat[base + i0]                                         # [points, d]
+    g1 = templ_flat[base + np.minimum(i0 + 1, lt - 1)]
+    g1 -= g0
+    g1 *= f
+    noise += g0
+    noise += g1
+    return noise
+
+
+# Every block of BLOCK consecutive series (database or queries) draws its
+# classes, warps, lengths and noise from its own stream, keyed by (seed,
+# role, block index), so that a database prefix or the queries can be drawn
+# without the rest and blocks can be drawn in parallel.
+BLOCK = 1024
+_DB, _QUERIES, _TEMPLATES = 1, 2, 0
+
+
+def _stream(seed: int, role: int, block: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence(seed,
+                                                                      spawn_key=(role, block))))
+
+
+def _block_header(g: np.random.Generator, count: int, n_classes: int, length,
+                  length_range):
+    classes = g.integers(0, n_classes, size=count).astype(np.int32)
+    knots = _warp_knots(g, count)
+    if length_range is None:
+        lens = np.full(count, int(length), dtype=np.int64)
+    else:
+        lens = g.integers(length_range[0], length_range[1] + 1, size=count).astype(np.int64)
+    return classes, knots, lens
+
+
+def _draw_set(seed: int, role: int, count: int, templ_flat: np.ndarray, lt: int, d: int,
+              n_classes: int, length, length_range, noise_sigma: float, threads: int):
+    """Series ``0 .. count-1`` of one role: (points [sum(len), d], offsets, classes)."""
+    nb = (count + BLOCK - 1) // BLOCK
+    heads = []
+    for b in range(nb):
+        c = min(BLOCK, count - b * BLOCK)
+        h = _block_header(_stream(seed, role, b), BLOCK, n_classes, length, length_range)
+        heads.append(tuple(x[:c] for x in h))
+    lens = np.concatenate([h[2] for h in heads]) if nb else np.zeros(0, np.int64)
+    classes = np.concatenate([h[0] for h in heads]) if nb else np.zeros(0, np.int32)
+    off = np.zeros(count + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    pts = np.empty((int(off[-1]), d), dtype=np.float32)
+
+    def fill(b):
+        g = _stream(seed, role, b)
+        c = min(BLOCK, count - b * BLOCK)
+        # the header is drawn for a whole block, so a partial last block
+        # draws the same values as the full one
+        cl, kn, ln = _block_header(g, BLOCK, n_classes, length, length_range)
+        cl, kn, ln = cl[:c], kn[:c], ln[:c]
+        noise = g.standard_normal((int(ln.sum()), d), dtype=np.float32)
+        noise *= np.float32(noise_sigma)
+        pts[off[b * BLOCK]: off[b * BLOCK + c]] = _resample(templ_flat, lt, cl, kn, ln, noise)
+
+    if nb:
+        with ThreadPoolExecutor(max_workers=max(1, min(threads, nb))) as ex:
+            list(ex.map(fill, range(nb)))
+    return pts, off, classes
 
 
 def make_workload(*, n_series: int, n_queries: int, d: int, length=64,
                   n_classes: int = 5, seed: int = 0, noise_sigma: float = 0.1,
                   correlated: bool = False, length_range: Optional[tuple] = None,
                   template_length: Optional[int] = None,
-                  batch: int = 16384) -> Workload:
+                  threads: Optional[int] = None) -> Workload:
     """Draw a seeded workload.
 
     ``length`` fixes every series length; ``length_range=(lo, hi)`` draws each
     length uniformly from the integers in [lo, hi] instead (both database and
-    queries).
+    queries).  Series i of the database depends only on (seed, i) and the
+    recipe, so a smaller ``n_series`` gives a prefix of the larger database;
+    the queries do not depend on ``n_series``.
     """
-    rng = np.random.Generator(np.random.PCG64(seed))
     lt = template_length or (length_range[1] if length_range else length)
-    templ = _templates(rng, n_classes, lt, d, correlated)
-    total = n_series + n_queries
-    classes = rng.integers(0, n_classes, size=total).astype(np.int32)
-    knots = _warp_knots(rng, total)
-    if length_range is None:
-        lens = np.full(total, int(length), dtype=np.int64)
-    else:
-        lens = rng.integers(length_range[0], length_range[1] + 1, size=total).astype(np.int64)
-    off = np.zeros(total + 1, dtype=np.int64)
-    np.cumsum(lens, out=off[1:])
-    pts = np.empty((int(off[-1]), d), dtype=np.float32)
-    if length_range is None:
-        for s in range(0, total, batch):
-            e = min(total, s + batch)
-            nz = rng.standard_normal((e - s, int(length), d)) * noise_sigma
-            inst = _instances(templ, classes[s:e], knots[s:e], int(length), nz)
-            pts[off[s]:off[e]] = inst.reshape(-1, d).astype(np.float32)
-    else:
-        # noise for all series in order, then one vectorised resampling per
-        # distinct length (same values as drawing series by series)
-        noise = rng.standard_normal((int(off[-1]), d)) * noise_sigma
-        for n in np.unique(lens):
-            idx = np.nonzero(lens == n)[0]
-            for s0 in range(0, len(idx), batch):
-                sel = idx[s0:s0 + batch]
-                nz = np.stack([noise[off[i]:off[i + 1]] for i in sel])
-                inst = _instances(templ, classes[sel], knots[sel], int(n), nz)
-                for j, i in enumerate(sel):
-                    pts[off[i]:off[i + 1]] = inst[j].astype(np.float32)
-    db_end = int(off[n_series])
+    templ = _templates(_stream(seed, _TEMPLATES), n_classes, lt, d, correlated)
+    templ_flat = np.ascontiguousarray(templ.reshape(-1, d), dtype=np.float32)
+    threads = threads or min(32, os.cpu_count() or 1)
+    db, db_off, db_lab = _draw_set(seed, _DB, n_series, templ_flat, lt, d, n_classes, length,
+                                   length_range, noise_sigma, threads)
+    q, q_off, q_lab = _draw_set(seed, _QUERIES, n_queries, templ_flat, lt, d, n_classes, length,
+                                length_range, noise_sigma, threads)
     return Workload(
-        d=d,
-        db=pts[:db_end],
-        db_off=off[:n_series + 1].copy(),
-        db_labels=classes[:n_series].copy(),
-        q=pts[db_end:],
-        q_off=off[n_series:] - off[n_series],
-        q_labels=classes[n_series:].copy(),
+        d=d, db=db, db_off=db_off, db_labels=db_lab, q=q, q_off=q_off, q_labels=q_lab,
         meta=dict(seed=seed, n_classes=n_classes, noise_sigma=noise_sigma,
                   correlated=correlated, length=length, length_range=length_range),
     )
@@ -178,19 +219,14 @@ def make_long_series(*, n: int, n_queries: int, d: int, q_length: int, n_classes
     rng = np.random.Generator(np.random.PCG64(seed))
     lt = 2 * q_length
     templ = _templates(rng, n_classes, lt, d, False)
+    tflat = np.ascontiguousarray(templ.reshape(-1, d), dtype=np.float32)
     chunks, total, last = [], 0, None
     while total < n:
         lens = rng.integers(q_length // 2, 2 * q_length + 1, size=batch)
         classes = rng.integers(0, n_classes, size=batch).astype(np.int32)
         knots = _warp_knots(rng, batch)
-        inst = [None] * batch
-        for L in np.unique(lens):
-            sel = np.nonzero(lens == L)[0]
-            nz = rng.standard_normal((len(sel), int(L), d)) * noise_sigma
-            block = _instances(templ, classes[sel], knots[sel], int(L), nz)
-            for j, i in enumerate(sel):
-                inst[i] = block[j]
-        chunk = np.concatenate(inst)
+        nz = (rng.standard_normal((int(lens.sum()), d)) * noise_sigma).astype(np.float32)
+        chunk = _resample(tflat, lt, classes, knots, lens, nz)
         if last is not None:          # continue from where the previous chunk ended
             chunk = chunk - chunk[0] + last
         last = chunk[-1]
@@ -200,8 +236,8 @@ def make_long_series(*, n: int, n_queries: int, d: int, q_length: int, n_classes
     t = pieces_all[:n].astype(np.float32)
     qc = rng.integers(0, n_classes, size=n_queries).astype(np.int32)
     qk = _warp_knots(rng, n_queries)
-    nz = rng.standard_normal((n_queries, q_length, d)) * noise_sigma
-    q = _instances(templ, qc, qk, q_length, nz).reshape(-1, d).astype(np.float32)
+    nz = (rng.standard_normal((n_queries * q_length, d)) * noise_sigma).astype(np.float32)
+    q = _resample(tflat, lt, qc, qk, np.full(n_queries, q_length), nz)
     q_off = np.arange(n_queries + 1, dtype=np.int64) * q_length
     return LongSeries(d=d, t=t, q=q, q_off=q_off,
                       meta=dict(seed=seed, n_classes=n_classes, q_length=q_length))
