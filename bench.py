@@ -1,19 +1,32 @@
 #!/usr/bin/env python
-"""Benchmark: exact k-NN scan (DTW and DK) on the d=3, 100,000 x 256 workload.
+"""Benchmark: exact k-NN scan (DTW and DK), learned + batched, on the d = 16,
+500,000 x 512 workload.
 
 One step = one batched scan of the step's 1,000 queries (per GPU) against the
-100,000-series database, for DTW and for DK (k = 10, Sakoe-Chiba band 10%),
-through the library's public C-ABI, inputs already resident in HBM.  Prints
-one JSON line (rank 0).
+500,000-series database (AR(1) correlated channels, d = 16, length 512), for
+DTW and for DK (k = 50, Sakoe-Chiba band 10%), with learned seeding, through
+the library's public C-ABI, inputs already resident in HBM.  The timed scans
+are the production path (no per-stage events); the stage split comes from one
+extra profiled scan per distance after the timed region.  Prints one JSON
+line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                    [--workload NAME]
 
 Under torchrun (N > 1) every rank scans its own 1,000 queries against a
 replica of the database (independent problems, no data-path collective);
 value = all ranks' queries / the slowest rank's time.
 
+The line also carries: the plain GPU scan (batched, LB_Box-ordered seeding,
+no encoder) and the paper's greedy pre-pass timed the same way on the same
+queries; a parity check (the oracle's exact result on a slice of the
+database against the GPU's on the same slice, and the oracle's distances for
+a sample of the full-size results); the oracle's CPU rate.
+
 --impl reference times the FP64 oracle (the paper's pruned scan, CPU) on a
-bounded sample of the same workload on the host cores.
+bounded sample of the same workload on the host cores: a fixed prefix of the
+database (the workload's first `oracle_series` series) and one query per
+core, extrapolated linearly to the whole database.
 """
 from __future__ import annotations
 
@@ -33,19 +46,24 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "exact k-NN queries/sec and DP GCUPS (DTW & DK), learned+batched vs plain GPU scan"
-# Workloads this harness measures (the first is the default and the headline):
-# generator name in synthdata.WORKLOADS, k, band, queries per GPU, whether the
-# timed scans replay a CUDA graph.
+# Workloads this harness measures: generator name in synthdata.WORKLOADS, k,
+# band, queries per GPU, whether the timed scans replay a CUDA graph, and the
+# database prefix the oracle scans for the CPU rate and the exact parity check.
 BENCH = {
-    "scale_d3_n100k_L256": dict(k=10, band=0.1, queries=1000, graph=False),
-    **{f"uneven_d{d}_n200k_L50_1000": dict(k=5, band=0.1, queries=256, graph=True)
+    "highdim_d16_n500k_L512": dict(k=50, band=0.1, queries=1000, graph=False,
+                                   oracle_series=4000),
+    "scale_d3_n100k_L256": dict(k=10, band=0.1, queries=1000, graph=False,
+                                oracle_series=100_000),
+    **{f"uneven_d{d}_n200k_L50_1000": dict(k=5, band=0.1, queries=256, graph=True,
+                                           oracle_series=20_000)
        for d in range(3, 9)},
-    "learned_d3_n1M_L128": dict(k=10, band=0.1, queries=1000, graph=False),
-    "highdim_d16_n500k_L512": dict(k=50, band=0.1, queries=32, graph=False),
+    "learned_d3_n1M_L128": dict(k=10, band=0.1, queries=1000, graph=False,
+                                oracle_series=50_000),
 }
-WORKLOAD = "scale_d3_n100k_L256"
-N_SERIES, LENGTH, D, N_QUERIES = 100_000, 256, 3, 1000
-K, BAND = 10, 0.1
+WORKLOAD = "highdim_d16_n500k_L512"
+N_SERIES, LENGTH, D, N_QUERIES = 500_000, 512, 16, 1000
+K, BAND = 50, 0.1
+ORACLE_SERIES = 4000
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 SEED_DESC = {"greedy": "greedy upper-bound pre-pass over every series (Section 4.3)",
@@ -55,6 +73,9 @@ SEED_DESC = {"greedy": "greedy upper-bound pre-pass over every series (Section 4
                         "LB_Box stream with early abandoning",
              "none": "no seeding"}
 TRAIN_PAIRS = 200_000
+# sampled full-size parity: queries checked, random other series per query
+PARITY_QUERIES, PARITY_OTHERS = 8, 192
+TOL = {0: 1e-5, 1: 1e-6}     # relative distance tolerance, DTW / DK
 
 
 # DRAM bytes (read + write) per launch of the dominant kernels on the bench
@@ -62,10 +83,6 @@ TRAIN_PAIRS = 200_000
 # captures of the current kernels (the summaries in profiles/ give the commands).
 # A kernel changed since its capture has no entry (traffic null).
 TRAFFIC = {
-    # mean of the DTW and DK launches of one scan, one-pass DRAM counters of
-    # the full workload
-    ("lb_compact_kernel", "scale_d3_n100k_L256"): 6.73e9,
-    ("dp_kernel", "scale_d3_n100k_L256"): 2.49e9,
     ("subseq_kernel", "subseq_d1_T1M_m256"): 5.78e6,
 }
 
@@ -137,79 +154,170 @@ class ClockSampler:
 
 def select_workload(name: str):
     """Set the module-level workload parameters from the BENCH table."""
-    global WORKLOAD, N_SERIES, LENGTH, D, N_QUERIES, K, BAND
+    global WORKLOAD, N_SERIES, LENGTH, D, N_QUERIES, K, BAND, ORACLE_SERIES
     from synthdata import WORKLOADS
     g, b = WORKLOADS[name], BENCH[name]
     WORKLOAD = name
     N_SERIES, D, N_QUERIES = g["n_series"], g["d"], b["queries"]
     LENGTH = g.get("length", 0) if "length_range" not in g else 0
     K, BAND = b["k"], b["band"]
+    ORACLE_SERIES = b["oracle_series"]
 
 
-def workload(world: int):
+def workload(world: int, n_series: int = 0):
+    """The workload (all ranks' queries); n_series > 0 draws only that prefix
+    of the database (the queries do not depend on it)."""
     from synthdata import WORKLOADS, make_workload
     kw = dict(WORKLOADS[WORKLOAD])
     kw["n_queries"] = N_QUERIES * world
-    kw["n_series"] = N_SERIES
+    kw["n_series"] = n_series or N_SERIES
     return make_workload(**kw)
 
 
-def cpu_baseline(w, n_sample: int = 0) -> dict:
-    """The FP64 oracle (paper's pruned scan) on a bounded sample of queries.
+def db_prefix(w, n: int):
+    """The first n series of a workload's database (points, offsets)."""
+    n = min(n, int(w.db_off.shape[0] - 1))
+    return w.db[: w.db_off[n]], w.db_off[: n + 1].copy()
 
-    The oracle runs one query per thread, so the sample is one query per host
-    core (n_sample = 0) and `cores` is the number of threads that worked."""
+
+def oracle_sample(w, n_sample: int, threads: int) -> dict:
+    """The FP64 oracle (the paper's pruned scan) on the first n_sample queries
+    against the first ORACLE_SERIES series, DTW and DK; returns the time, its
+    results and the extrapolation to the whole database."""
     import oracle
     oracle.lib()
-    n_sample = n_sample or (os.cpu_count() or 1)
-    n_sample = min(n_sample, int(w.q_off.shape[0] - 1))
-    cores = min(os.cpu_count() or 1, n_sample)
-    band = float(np.float32(BAND))
+    db, off = db_prefix(w, ORACLE_SERIES)
+    n_slice = int(off.shape[0] - 1)
     q_off = w.q_off[: n_sample + 1]
     q = w.q[: q_off[-1]]
+    band = float(np.float32(BAND))
+    res, cells = {}, 0
     t0 = time.perf_counter()
-    cells = 0
     for kind in (0, 1):
-        _, _, st = oracle.knn(w.db, w.db_off, q, q_off, band=band, kind=kind, k=K, method=True,
-                              threads=cores, with_stats=True)
+        ids, dist, st = oracle.knn(db, off, q, q_off, band=band, kind=kind, k=K, method=True,
+                                   threads=threads, with_stats=True)
+        res[kind] = (ids, dist)
         cells += int(st[:, 3].sum())
     dt = time.perf_counter() - t0
-    return {"value": 2 * n_sample / dt, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_sample} queries x {N_SERIES} series, DTW and DK, k={K}, band 10%, "
-                      f"FP64 pruned scan (LB_Box, GDK, sparse DK, early abandoning), "
-                      f"{cores} threads",
-            "seconds": dt, "dp_cells": cells}
+    scale = N_SERIES / n_slice
+    return {"seconds": dt, "results": res, "n_slice": n_slice, "dp_cells": cells,
+            "value": 2 * n_sample / (dt * scale)}
+
+
+def cpu_baseline(w, n_sample: int = 0) -> dict:
+    """The oracle as it stands, one query per host core, on the database
+    prefix, extrapolated linearly to all N_SERIES series; plus a single-core
+    figure (one query, one thread) as the paper reports one core."""
+    cores = os.cpu_count() or 1
+    n_sample = min(n_sample or cores, int(w.q_off.shape[0] - 1))
+    threads = min(cores, n_sample)
+    r = oracle_sample(w, n_sample, threads)
+    one = oracle_sample(w, 1, 1)
+    return {"value": r["value"], "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": f"{n_sample} queries x the first {r['n_slice']} of {N_SERIES} series, "
+                      f"DTW and DK, k={K}, band {BAND:g}, FP64 pruned scan (LB_Box, GDK, sparse "
+                      f"DK, early abandoning), {threads} threads, {r['seconds']:.1f} s; "
+                      f"queries/s extrapolated linearly in the number of series "
+                      f"(x{N_SERIES / r['n_slice']:.4g})",
+            "seconds": r["seconds"], "dp_cells": r["dp_cells"],
+            "single_core": {"value": one["value"], "unit": "queries/s", "cores": 1,
+                            "seconds": one["seconds"],
+                            "sample": f"1 query x {r['n_slice']} series, DTW and DK, "
+                                      f"extrapolated to {N_SERIES} series"},
+            "_results": r["results"], "_n_sample": n_sample}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w = workload(1)
-    # one query per host core per step (the oracle runs a query per thread)
+    # only the database prefix the oracle scans is drawn (series i depends on
+    # the seed and i alone, the queries on neither)
+    w = workload(1, ORACLE_SERIES)
     cores = os.cpu_count() or 1
     n_sample = min(args.cpu_sample or cores, N_QUERIES)
-    cores = min(cores, n_sample)
+    threads = min(cores, n_sample)
     for _ in range(args.warmup):
-        cpu_baseline(w, n_sample)
+        oracle_sample(w, n_sample, threads)
+    secs = 0.0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cpu_baseline(w, n_sample)
+        secs += oracle_sample(w, n_sample, threads)["seconds"]
     dt = time.perf_counter() - t0
-    value = 2 * n_sample * args.steps / dt
-    sample = f"{n_sample} queries x {N_SERIES} series per step, DTW and DK, k={K}, band 10%"
+    n_slice = min(ORACLE_SERIES, N_SERIES)
+    scale = N_SERIES / n_slice
+    value = 2 * n_sample * args.steps / (secs * scale)
+    sample = (f"{n_sample} queries x the first {n_slice} of {N_SERIES} series per step, DTW and "
+              f"DK, k={K}, band {BAND:g}, FP64 pruned scan, {threads} threads; queries/s "
+              f"extrapolated linearly in the number of series (x{scale:.4g})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH or "50-1000", "d": D,
-                       "k": K, "band": BAND, "sample_queries_per_step": n_sample},
-            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
+            "config": {"workload": WORKLOAD, "n_series": N_SERIES,
+                       "length": LENGTH or "50-1000", "d": D, "k": K, "band": BAND,
+                       "sample_queries_per_step": n_sample, "oracle_series": n_slice},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": threads,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def check_knn(ids, dist, oids, odist, kind) -> dict:
+    """GPU k-NN rows against the oracle's: identical ids in order, distances
+    within the relative tolerance of the distance."""
+    ids, dist = np.asarray(ids), np.asarray(dist, dtype=np.float64)
+    same_ids = bool(np.array_equal(ids, oids))
+    fin = np.isfinite(odist)
+    rel = np.abs(dist[fin] - odist[fin]) / np.maximum(np.abs(odist[fin]), 1e-30)
+    worst = float(rel.max()) if rel.size else 0.0
+    return {"ids_identical": same_ids, "max_rel_err": worst, "tol": TOL[kind],
+            "pass": same_ids and worst <= TOL[kind] and
+            bool(np.array_equal(np.isfinite(dist), fin))}
+
+
+def sampled_parity(w, kind, ids, dist, nq: int, n_others: int, seed: int = 0) -> dict:
+    """Full-size check on sampled outputs: for each of the first nq queries
+    the oracle computes (FP64) the distance of every returned series and of
+    n_others random other series.  Passes if the returned distances agree
+    within the tolerance, the rows are ordered by (distance, id), and no
+    sampled series is closer than the k-th result (ties by id)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    N = int(w.db_off.shape[0] - 1)
+    band = float(np.float32(BAND))
+    worst, ok = 0.0, True
+    for qi in range(nq):
+        got = [int(x) for x in ids[qi] if x >= 0]
+        others = [int(x) for x in rng.choice(N, size=min(n_others, N), replace=False)
+                  if int(x) not in set(got)]
+        sel = got + others
+        pts = [w.series(i) for i in sel]
+        b_off = np.zeros(len(sel) + 1, dtype=np.int64)
+        np.cumsum([len(p) for p in pts], out=b_off[1:])
+        b = np.concatenate(pts)
+        q = w.query(qi)
+        a_off = np.array([0, q.shape[0]], dtype=np.int64)
+        pa = np.zeros(len(sel), dtype=np.int64)
+        pb = np.arange(len(sel), dtype=np.int64)
+        od = oracle.pairwise(q, a_off, b, b_off, pa, pb, band=band, kind=kind)
+        gd = np.asarray(dist[qi][: len(got)], dtype=np.float64)
+        rel = np.abs(gd - od[: len(got)]) / np.maximum(np.abs(od[: len(got)]), 1e-30)
+        worst = max(worst, float(rel.max()) if rel.size else 0.0)
+        keys = list(zip(gd.tolist(), got))
+        ok &= keys == sorted(keys)
+        if len(got) == ids.shape[1]:
+            # a series outside the result is not closer than the k-th (equal
+            # distances are ordered by id, so only "clearly closer" fails)
+            kth = float(od[len(got) - 1])
+            ok &= bool(np.all(od[len(got):] >= kth * (1 - TOL[kind])))
+        else:
+            # fewer than k finite results: every sampled series is infinite
+            ok &= bool(np.all(~np.isfinite(od[len(got):])))
+    return {"queries": nq, "others_per_query": n_others, "max_rel_err": worst,
+            "tol": TOL[kind], "pass": bool(ok and worst <= TOL[kind])}
 
 
 def run_gpu(args):
@@ -226,12 +334,14 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     kw.lib()
 
+    t_setup = time.perf_counter()
     w = workload(world)
     nq = N_QUERIES
     (q0, q1), q_off = query_shard(w.q_off, rank, world, nq)
     q_host = np.ascontiguousarray(w.q[q0:q1])
     db_dev = torch.from_numpy(w.db).cuda()
     kinds = {"both": (kw.DTW, kw.DK), "dtw": (kw.DTW,), "dk": (kw.DK,)}[args.only]
+    kname = {kw.DTW: "DTW", kw.DK: "DK"}
     seed_mode = {"greedy": kw.SEED_GREEDY, "lb": kw.SEED_LB, "none": kw.SEED_NONE,
                  "learned": kw.SEED_LEARNED}[args.seed]
     # one database handle per distance: each carries the encoder trained on
@@ -241,25 +351,23 @@ def run_gpu(args):
         dbs[kind] = kw.KnnDB(db_dev, w.db_off)
         if args.seed == "learned":
             enc = kw.Encoder(D, seed=11 + kind)
-            train_info["DTW" if kind == kw.DTW else "DK"] = enc.train(
+            train_info[kname[kind]] = enc.train(
                 dbs[kind], TRAIN_PAIRS, epochs=3, batch_pairs=2048, lr=2e-3, distance=kind,
                 band=BAND, seed=5 + kind)
             enc.attach(dbs[kind])
             encoders[kind] = enc
-    db = dbs[kinds[0]]
+    del db_dev
     q_dev = torch.from_numpy(q_host).cuda()
     q_off_t = torch.from_numpy(q_off)
-    ids = torch.empty((nq, K), dtype=torch.int64, device="cuda")
-    dst = torch.empty((nq, K), dtype=torch.float32, device="cuda")
-    cnt = torch.empty(nq, dtype=torch.int64, device="cuda")
+    out = {kind: (torch.empty((nq, K), dtype=torch.int64, device="cuda"),
+                  torch.empty((nq, K), dtype=torch.float32, device="cuda"),
+                  torch.empty(nq, dtype=torch.int64, device="cuda")) for kind in kinds}
+    graph = BENCH[WORKLOAD]["graph"] and not args.no_graph
 
-    def step(collect=None):
-        for kind in kinds:
-            _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
-                                      seed=seed_mode, out=(ids, dst, cnt), stats=True,
-                                      profile=not graph, use_graph=graph)
-            if collect is not None:
-                collect.append((kind, st))
+    def scan(kind, mode=seed_mode, profile=False, o=None):
+        return dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=mode,
+                              out=o or out[kind], stats=True, profile=profile,
+                              use_graph=graph and not profile)
 
     def barrier():
         if world > 1:
@@ -269,7 +377,6 @@ def run_gpu(args):
     # autotuner (set-up, outside the timed region): DP shape per distance
     shapes = {}
     r = int(np.float64(np.float32(BAND)) * LENGTH)
-    graph = BENCH[WORKLOAD]["graph"] and not args.no_graph
     for kind in kinds:
         if args.lb_compaction or args.lb_qtile:
             dbs[kind].set_lb_tile(kind, args.lb_qtile, 0, args.lb_compaction)
@@ -281,11 +388,15 @@ def run_gpu(args):
             dbs[kind].autotune(q_dev[: int(q_off[nt])], q_off_t[: nt + 1], k=K, band=BAND,
                                distance=kind, seed=seed_mode)
         if LENGTH:
-            shapes["DTW" if kind == kw.DTW else "DK"] = dict(
-                zip(("P", "G"), dbs[kind].get_dp_shape(kind, r, LENGTH)))
+            shapes[kname[kind]] = dict(zip(("P", "G"), dbs[kind].get_dp_shape(kind, r, LENGTH)))
+    setup_s = time.perf_counter() - t_setup
 
-    for _ in range(max(args.warmup, 3)):
-        step()
+    # warm-up, then the timed steps: the production path (no stage events;
+    # the counters come back with the status word every scan reads anyway)
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        for kind in kinds:
+            scan(kind)
     collected = []
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -293,60 +404,50 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            step(collected)
+            for kind in kinds:
+                collected.append((kind, scan(kind)[2]))
         e1.record(stream)
         barrier()
     ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
     total_queries = nq * len(kinds) * args.steps * world
     value = total_queries / (ms / 1000.0)
+    headline = {kind: (out[kind][0].clone(), out[kind][1].clone()) for kind in kinds}
 
-    if graph:
-        # the timed scans replayed graphs (no events inside); take the stage
-        # split from one profiled eager scan per distance
-        prof = []
-        for kind in kinds:
-            _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
-                                      seed=seed_mode, out=(ids, dst, cnt), stats=True,
-                                      profile=True)
-            prof.append((kind, st))
-        for i, (kind, st) in enumerate(collected):
-            p = dict(prof[[k_ for k_, _ in prof].index(kind)][1])
-            scale = st["ms_total"] / max(p["ms_total"], 1e-9)
-            for key in ("ms_seed", "ms_lb", "ms_dp", "ms_finalize"):
-                st[key] = p[key] * scale
-    # per-distance detail (this rank)
+    # stage split: one profiled eager scan per distance, outside the timed region
+    prof = {kind: scan(kind, profile=True)[2] for kind in kinds}
     detail = {}
     for kind in kinds:
         sts = [s for k_, s in collected if k_ == kind]
         agg = {key: sum(s[key] for s in sts) for key in sts[0]}
-        name = "DTW" if kind == kw.DTW else "DK"
-        detail[name] = {
+        p = prof[kind]
+        ms_scan = agg["ms_total"] / len(sts)
+        detail[kname[kind]] = {
             "queries_per_s": nq * len(sts) / (agg["ms_total"] / 1000.0),
-            "dp_gcups": agg["dp_cells"] / (agg["ms_dp"] / 1000.0) / 1e9 if agg["ms_dp"] else None,
-            "ms_per_scan": agg["ms_total"] / len(sts),
-            "ms_seed": agg["ms_seed"] / len(sts), "ms_lb": agg["ms_lb"] / len(sts),
-            "ms_dp": agg["ms_dp"] / len(sts), "ms_finalize": agg["ms_finalize"] / len(sts),
+            "ms_per_scan": ms_scan,
+            "dp_gcups": p["dp_cells"] / (p["ms_dp"] / 1000.0) / 1e9 if p["ms_dp"] else None,
+            "profiled_scan": {key: p[key] for key in ("ms_total", "ms_seed", "ms_lb", "ms_dp",
+                                                      "ms_finalize")},
             "dp_calls_per_query": agg["dp_calls"] / (nq * len(sts)),
             "dp_abandoned_frac": agg["dp_abandoned"] / max(agg["dp_calls"], 1),
             "lb_pruned_frac": (agg["lb_pruned"] + agg["lb_pruned_late"]) / max(agg["pairs"], 1),
             "dp_cells_per_query": agg["dp_cells"] / (nq * len(sts)),
             "seed_cells_per_query": agg["seed_cells"] / (nq * len(sts)),
-            "reranked": agg["reranked"],
+            "reranked": agg["reranked"] // len(sts),
         }
     launches = sum(s["launches"] for _, s in collected)
 
-    # roofline of the dominant kernel (largest share of stage time).  Both
-    # stages are plain FP32-ALU work: the LB_Box stream with a tile of queries
-    # per pass does 4 lane operations per (query, element) it evaluates (max,
-    # min, sub, FMA; the DK max form adds one max per point), the DP 2d+3 per
-    # band cell.  Peak = SMs x 128 FP32 lanes x the maximum SM clock.
+    # roofline of the dominant kernel (largest share of the profiled scans'
+    # stage time).  Both stages are plain FP32-ALU work: the LB_Box stream with
+    # a tile of queries per pass does 4 lane operations per (query, element)
+    # it evaluates (two subtractions, a max, an FMA; the DK max form adds one
+    # max per point), the DP 2d+3 per band cell.  Peak = SMs x 128 FP32 lanes
+    # x the maximum SM clock.
     hbm_gbs, sm_max_mhz, peak_src = peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
     stage = {"seed": 0.0, "lb": 0.0, "dp": 0.0, "finalize": 0.0}
     dp_ops = lb_ops = 0.0
-    lb_launches = dp_launches = 0
-    for kind, s in collected:
+    for kind, s in prof.items():
         for k_ in stage:
             stage[k_] += s[f"ms_{k_}"]
         dp_ops += s["dp_cells"] * (2 * D + 3)
@@ -360,18 +461,16 @@ def run_gpu(args):
               "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
               "traffic": TRAFFIC.get((kernel, WORKLOAD)),
               "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
-                             f"(max SM clock, {peak_src})"}
+                             f"(max SM clock, {peak_src})",
+              "timing": "CUDA events around the stage in one profiled scan per distance"}
         if clocks.get("sm_mhz"):
             r_["frac_at_sampled_clock"] = achieved / (n_sm * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
         return r_
 
     # which LB_Box kernels ran (the library reports a bit mask per scan)
     lb_bits = 0
-    for _, s in collected:
+    for s in list(prof.values()) + [s for _, s in collected]:
         lb_bits |= int(s.get("lb_kernels", 0))
-    if graph:
-        for _, s in prof:
-            lb_bits |= int(s.get("lb_kernels", 0))
     lb_name = "+".join(n_ for b_, n_ in ((1, "lb_kernel"), (2, "lb_multi_kernel"),
                                          (4, "lb_win_kernel"), (8, "lb_compact_kernel"))
                        if lb_bits & b_) or "lb_multi_kernel"
@@ -394,7 +493,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         for kind in kinds:
             dbs[kind].scan(q_pin, q_off_t, k=K, band=BAND, distance=kind, seed=seed_mode,
-                           out=(ids_h, dst_h, cnt_h))
+                           out=(ids_h, dst_h, cnt_h), use_graph=graph)
     barrier()
     e2e_dt = max_over_ranks(time.perf_counter() - t0, device="cuda")
     h2d = (q_host.nbytes + q_off.nbytes) * len(kinds)
@@ -402,65 +501,120 @@ def run_gpu(args):
     e2e = {"value": nq * len(kinds) * e2e_steps * world / e2e_dt, "unit": "queries/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # the plain form: one query per launch sequence, first 50 queries
-    plain = {}
-    if rank == 0 and not args.no_plain:
-        nplain = min(50, nq)
-        qp = q_dev[: int(q_off[nplain])]
-        qpo = q_off_t[: nplain + 1]
-        for kind in kinds:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dbs[kind].scan(qp, qpo, k=K, band=BAND, distance=kind, query_batch=1,
-                           seed=kw.SEED_GREEDY)
-            torch.cuda.synchronize()
-            plain["DTW" if kind == kw.DTW else "DK"] = nplain / (time.perf_counter() - t0)
-
-    # every seeding mode once on the same batch (same results; work and time)
-    variants = {}
+    # the comparators, timed like the headline (CUDA events around whole
+    # scans on the same queries, same tuned shapes): the plain GPU scan
+    # (batched, LB_Box-ordered seeding, no encoder), the paper's greedy
+    # pre-pass (Section 4.3), and the same learned flow with an untrained
+    # encoder (what the training itself buys)
+    comparators = {}
     if rank == 0 and not args.no_variants:
-        modes = [("greedy", kw.SEED_GREEDY), ("lb", kw.SEED_LB)]
+        n_cmp = max(1, min(args.steps, 2))
+        cmp_db = None
         if args.seed == "learned":
-            modes.append(("learned", kw.SEED_LEARNED))
+            cmp_db = kw.KnnDB(w.db, w.db_off)
+            untrained = kw.Encoder(D, seed=99)
+            untrained.attach(cmp_db)
+        modes = [("plain_lb", kw.SEED_LB, None), ("greedy", kw.SEED_GREEDY, None)]
+        if cmp_db is not None:
+            modes.append(("learned_untrained", kw.SEED_LEARNED, cmp_db))
         for kind in kinds:
-            kname = "DTW" if kind == kw.DTW else "DK"
-            ref = None
-            for mname, mode in modes:
-                dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=mode,
-                               out=(ids, dst, cnt))  # warm
-                _, _, st = dbs[kind].scan(q_dev, q_off_t, k=K, band=BAND, distance=kind,
-                                          seed=mode, out=(ids, dst, cnt), stats=True,
-                                          profile=True)
-                res = (ids.clone(), dst.clone())
-                same = ref is None or (torch.equal(ref[0], res[0]) and
-                                       torch.equal(ref[1], res[1]))
-                ref = ref or res
-                variants[f"{kname}/{mname}"] = {
-                    "queries_per_s": nq / (st["ms_total"] / 1000.0), "identical_results": same,
-                    "ms_seed": st["ms_seed"], "ms_lb": st["ms_lb"], "ms_dp": st["ms_dp"],
-                    "ub_walks": st["ub_walks"], "lb_points": st["lb_points"],
-                    "dp_calls": st["dp_calls"], "dp_cells": st["dp_cells"] + st["seed_cells"]}
+            for mname, mode, other in modes:
+                h = other or dbs[kind]
+                if other is not None:
+                    h.set_lb_tile(kind, *dbs[kind].get_lb_tile(kind))
+                    if LENGTH:
+                        h.set_dp_shape(kind, r, LENGTH, *dbs[kind].get_dp_shape(kind, r, LENGTH))
+                o = (torch.empty_like(out[kind][0]), torch.empty_like(out[kind][1]),
+                     torch.empty_like(out[kind][2]))
+                h.scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=mode, out=o)
+                st_sum = None
+                torch.cuda.synchronize()
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                for _ in range(n_cmp):
+                    _, _, st = h.scan(q_dev, q_off_t, k=K, band=BAND, distance=kind, seed=mode,
+                                      out=o, stats=True)
+                    st_sum = st if st_sum is None else {k_: st_sum[k_] + st[k_] for k_ in st}
+                c1.record(stream)
+                c1.synchronize()
+                cms = c0.elapsed_time(c1)
+                same = bool(torch.equal(o[0], headline[kind][0]) and
+                            torch.equal(o[1], headline[kind][1]))
+                comparators[f"{kname[kind]}/{mname}"] = {
+                    "queries_per_s": nq * n_cmp / (cms / 1000.0), "scans_timed": n_cmp,
+                    "identical_results": same,
+                    "ub_walks": st_sum["ub_walks"] // n_cmp,
+                    "lb_points": st_sum["lb_points"] // n_cmp,
+                    "dp_calls": st_sum["dp_calls"] // n_cmp,
+                    "dp_cells": (st_sum["dp_cells"] + st_sum["seed_cells"]) // n_cmp}
+        if cmp_db is not None:
+            cmp_db.close()
+            untrained.close()
+    headline_cmp = {}
+    for kind in kinds:
+        base = comparators.get(f"{kname[kind]}/plain_lb")
+        if base:
+            headline_cmp[kname[kind]] = detail[kname[kind]]["queries_per_s"] / base["queries_per_s"]
 
+    line = None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
-            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_series": N_SERIES, "length": LENGTH or "50-1000", "d": D,
-                       "queries_per_gpu": nq, "k": K, "band": BAND,
-                       "distances": ["DTW" if k_ == kw.DTW else "DK" for k_ in kinds],
-                       "seed": SEED_DESC[args.seed], "cuda_graph": graph,
-                       "batched": True,
+            "config": {"workload": WORKLOAD, "n_series": N_SERIES,
+                       "length": LENGTH or "50-1000", "d": D, "queries_per_gpu": nq, "k": K,
+                       "band": BAND, "distances": [kname[k_] for k_ in kinds],
+                       "seed": SEED_DESC[args.seed], "cuda_graph": graph, "batched": True,
                        "l2": f"inputs larger than L2 ({w.db.nbytes / 1e6:.0f} MB database)",
                        "parallelism": f"replicated database, queries sharded x{world}"},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
-            "per_distance": detail, "plain_scan_queries_per_s": plain, "dp_shape": shapes,
-            "seed_variants": variants, "encoder_training": train_info,
+            "per_distance": detail, "vs_plain_gpu_scan": headline_cmp,
+            "comparators": comparators, "dp_shape": shapes, "encoder_training": train_info,
+            "setup_s": setup_s,
         }
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_sample)
+
+    # parity of the measured configuration against the oracle
+    if rank == 0 and not args.no_parity:
+        par = {}
+        hcpu = {kind: (headline[kind][0].cpu().numpy(), headline[kind][1].cpu().numpy())
+                for kind in kinds}
+        for kind in kinds:
+            par[f"{kname[kind]}/full_size_sampled"] = sampled_parity(
+                w, kind, *hcpu[kind], min(PARITY_QUERIES, nq), PARITY_OTHERS, seed=kind)
+        line["parity"] = par
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, args.cpu_sample)
+        res, ns = cb.pop("_results"), cb.pop("_n_sample")
+        line["cpu_baseline"] = cb
+        if not args.no_parity:
+            # the GPU on the same database prefix and queries, same flow
+            sdb_pts, sdb_off = db_prefix(w, ORACLE_SERIES)
+            full = sdb_off.shape[0] - 1 >= N_SERIES
+            for kind in kinds:
+                if full:
+                    gi, gd = (x[:ns] for x in hcpu[kind])
+                else:
+                    sdb = kw.KnnDB(sdb_pts, sdb_off)
+                    if kind in encoders:
+                        encoders[kind].attach(sdb)
+                    gi, gd = sdb.scan(q_dev[: int(q_off[ns])], q_off_t[: ns + 1], k=K,
+                                      band=BAND, distance=kind, seed=seed_mode)
+                    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+                    sdb.close()
+                c = check_knn(gi, gd, *res[kind], kind)
+                c.update(queries=ns, series=int(sdb_off.shape[0] - 1))
+                line["parity"][f"{kname[kind]}/database_prefix_exact"] = c
+        line["parity"]["pass"] = all(v["pass"] for v in line["parity"].values()
+                                     if isinstance(v, dict))
+    elif rank == 0 and not args.no_parity:
+        line["parity"]["pass"] = all(v["pass"] for v in line["parity"].values())
+    if rank == 0:
         print(json.dumps(line), flush=True)
+    for e_ in encoders.values():
+        e_.close()
     for d_ in dbs.values():
         d_.close()
     if world > 1:
@@ -676,8 +830,10 @@ def main():
                     help="queries of the oracle's timed sample (0: one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
-    ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the comparators (plain GPU scan, greedy, untrained encoder)")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the oracle checks of the measured results")
     from synthdata import LONG_SERIES
     ap.add_argument("--workload", default=WORKLOAD, choices=list(BENCH) + list(LONG_SERIES))
     ap.add_argument("--queries", type=int, default=0,
