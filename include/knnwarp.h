@@ -62,7 +62,7 @@ typedef enum {
     KNN_ERR_CUDA = 3,        /* a CUDA call failed                               */
     KNN_ERR_TIMEOUT = 4,     /* a bounded device wait gave up                    */
     KNN_ERR_CAPACITY = 5,    /* eps-NN result larger than eps_capacity; counts
-                                hold the true sizes                              */
+                                bound the sizes (see knn_scan)                   */
     KNN_ERR_UNSUPPORTED = 6  /* configuration not compiled in (e.g. d > 16)     */
 } knn_status;
 
@@ -97,7 +97,9 @@ typedef struct {
     int32_t query_batch;   /* queries per launch sequence; 0 = all in one batch      */
     int32_t use_graph;     /* 1 = capture each batch's launch sequence in a CUDA
                               graph and replay it (cached per database and shape)    */
-    int64_t eps_capacity;  /* eps-NN: result slots per query                         */
+    int64_t eps_capacity;  /* eps-NN: result slots per query, 1 .. 2^24 (above 8,192
+                              the lists are sorted in global memory; the scratch
+                              is 3 x 8 bytes per slot and query)                     */
     int32_t profile;       /* 1 = time each stage with CUDA events (stats->ms_*);
                               ignored when use_graph = 1                             */
     int32_t reserved;
@@ -115,7 +117,11 @@ typedef struct {
     int64_t lb_pruned_late;  /* pruned by LB_Box at DP start (tighter threshold) */
     int64_t dp_calls;        /* dynamic programs started                         */
     int64_t dp_abandoned;    /* dynamic programs abandoned early                 */
-    int64_t dp_cells;        /* band cells evaluated (lane slots x steps)        */
+    int64_t dp_cells;        /* band cells of the m x n matrices evaluated: every
+                                cell of a finished pair, and the cells on the
+                                anti-diagonals swept before an abandoned pair
+                                was dropped (lane slots outside the band and
+                                the virtual prefix are not counted)              */
     int64_t reranked;        /* candidates re-scored in FP64                     */
     int64_t lb_points;       /* (query, series point) pairs bounded by LB_Box    */
     int64_t launches;        /* kernels launched by the call                     */
@@ -157,8 +163,17 @@ KNN_API knn_status knn_db_info(const knn_db *db, int64_t *n_series, int32_t *d,
  *   k-NN:   out_ids [n_queries][k], out_dist [n_queries][k]; out_counts may
  *           be NULL (else receives the number of finite results per query).
  *   eps-NN: out_ids/out_dist [n_queries][eps_capacity], out_counts
- *           [n_queries] (true result sizes; KNN_ERR_CAPACITY if one exceeds
- *           eps_capacity, with the first eps_capacity results written).
+ *           [n_queries] (result sizes).  The result SET is exact; rows are
+ *           ordered by the reported distances, which never decrease (FP32,
+ *           or FP64 where re-scored near eps), so two results whose exact
+ *           distances lie within the FP32 error band of each other may
+ *           appear in either order.  If a row holds more results than
+ *           eps_capacity the call returns KNN_ERR_CAPACITY: that row's
+ *           stored entries are true results (padded with -1 / +inf where
+ *           some were dropped at eps) and its count is an upper bound of its
+ *           size, above it only by results within the FP32 error band of
+ *           eps that could not be stored and re-checked; a retry with that
+ *           capacity holds the row.  k-NN rows are in exact order.
  *   stats may be NULL. */
 KNN_API knn_status knn_scan(knn_db *db, const float *queries, const int64_t *q_offsets,
                             int32_t n_queries, const knn_params *params,
@@ -274,10 +289,14 @@ KNN_API knn_status knn_pairwise(const float *a, const int64_t *a_off, const floa
  * padded sizes) and nothing is computed.  All pointers are device memory;
  * a_off / b_off have n_a + 1 / n_b + 1 point offsets; out receives n_pairs
  * floats.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make it before capturing
- * any stream.  Every call shares the array and clears its counters; calls
- * that overlap on the GPU race and must be serialised by the caller.  The
- * call synchronises `stream` before returning. */
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; after the device's primary context is destroyed
+ * (cudaDeviceReset) the function must not be called on that device again.
+ * Every call shares the array and clears its counters; calls that overlap on
+ * the GPU race and must be serialised by the caller.  The call reads its
+ * status back and synchronises `stream` before returning, so it cannot be
+ * captured into a CUDA graph: on a stream under capture it returns
+ * KNN_ERR_INVALID without touching the stream. */
 KNN_API knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off, int64_t n_a,
                                         const float *b, const int64_t *b_off, int64_t n_b,
                                         const int64_t *pa, const int64_t *pb, int64_t n_pairs,

@@ -81,14 +81,44 @@ bool knn::is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Fault injection for tests (host side, no GPU fault): KNN_FAULT_INJECT=alloc
+// fails every device allocation of the library; alloc_after:N lets N more
+// allocations succeed (counted from the first allocation that sees this
+// value) and fails the ones after.
+static bool alloc_fault_injected()
+{
+    static std::mutex mu;
+    static std::string seen;
+    static long remaining = 0;
+    const char *f = getenv("KNN_FAULT_INJECT");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!f) {
+        seen.clear();
+        return false;
+    }
+    if (!strcmp(f, "alloc"))
+        return true;
+    if (!strncmp(f, "alloc_after:", 12)) {
+        if (seen != f) {
+            seen = f;
+            remaining = strtol(f + 12, nullptr, 10);
+        }
+        if (remaining > 0) {
+            --remaining;
+            return false;
+        }
+        return true;
+    }
+    return false;
+}
+
 knn_status DevBuf::ensure(size_t b)
 {
     if (b <= bytes)
         return KNN_OK;
     release();
-    if (const char *f = getenv("KNN_FAULT_INJECT"))
-        if (!strcmp(f, "alloc"))
-            return set_error(KNN_ERR_OOM, "allocation failure injected (KNN_FAULT_INJECT=alloc)");
+    if (alloc_fault_injected())
+        return set_error(KNN_ERR_OOM, "allocation failure injected (KNN_FAULT_INJECT)");
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
         p = nullptr;

@@ -347,7 +347,10 @@ extern "C" knn_status knn_pairwise(const float *a, const int64_t *a_off, const f
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const int occ = dp_max_blocks_per_sm(deff, P, distance);
-        launch_dp(x, deff, P, distance, nsm * std::max(occ, 1), st);
+        if (!launch_dp(x, deff, P, distance, nsm * std::max(occ, 1), st)) {
+            cudaStreamSynchronize(st);
+            return set_error(KNN_ERR_UNSUPPORTED, "no DP kernel compiled for this d and shape");
+        }
         pair_out_kernel<<<256, 256, 0, st>>>(OUT.as<float>(), n_pairs, distance, out_f32);
         e = cudaStreamSynchronize(st);
         if (e == cudaSuccess)

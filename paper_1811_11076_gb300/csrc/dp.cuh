@@ -357,13 +357,16 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
             } else if (mn > lim) {
                 if (lam == 0) {
                     st_aband += 1;
-                    long long full = 0;
-                    long long part = (long long)(2 * s0) * (2 * r + 1) / 2;
+                    // exact band cells on the anti-diagonals t = i + j < 2 s0
+                    // swept so far (diagonal dlt: rows i with 2i + dlt < 2 s0)
+                    long long swept = 0;
                     for (int dlt = -r; dlt <= r; ++dlt) {
                         const int hi = min(m, n - dlt), loi = max(0, -dlt);
-                        full += max(0, hi - loi);
+                        const int ub = 2 * s0 - dlt;
+                        const int ui = ub <= 0 ? 0 : (ub + 1) >> 1;
+                        swept += max(0, min(hi, ui) - loi);
                     }
-                    st_cells += part < full ? part : full;
+                    st_cells += swept;
                 }
                 active = false;
             }

@@ -297,23 +297,283 @@ __global__ void __launch_bounds__(FIN_THREADS) fin_out_kernel(const FinArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// eps-NN lists longer than the shared-memory sort holds (eps_cap above
+// FIN_SMALL_CAP): a merge sort in global memory (runs of FIN_RUN keys sorted
+// in shared memory, then merge passes), a mark pass over the sorted list, the
+// same FP64 re-scoring, and an output pass that re-orders only the tail of
+// the list near eps.  Keys are (FP32 value bits, id), unique per query.
+
+constexpr int FIN_RUN = 4096;           // keys per run sorted in shared memory
+constexpr int FIN_RUN_THREADS = 512;
+constexpr int FIN_MERGE_PER_THREAD = 8; // consecutive outputs per merge thread
+constexpr int FIN_MERGE_THREADS = 256;
+constexpr int FIN_MERGE_TILE = FIN_MERGE_PER_THREAD * FIN_MERGE_THREADS;
+constexpr int FIN_TAIL_CAP = 8192;      // keys near eps re-ordered in shared memory
+
+__device__ __forceinline__ int fin_list_len(const int *eps_count, int cap, int qb)
+{
+    return min(eps_count[qb], cap);
+}
+
+// Lower edge of the tail that may be re-ordered: FP32 values below it are
+// more than the FP32 error band below every re-scored value.
+__device__ __forceinline__ float fin_tail_lo(const FinArgs &a)
+{
+    return a.eps_int * (1.f - 2.f * a.rerank_rel);
+}
+
+__global__ void __launch_bounds__(FIN_RUN_THREADS) fin_run_sort_kernel(const FinArgs a)
+{
+    __shared__ unsigned long long keys[FIN_RUN];
+    const int qb = blockIdx.x;
+    const int cnt = fin_list_len(a.eps_count, a.eps_cap, qb);
+    const int r0 = blockIdx.y * FIN_RUN;
+    if (r0 >= cnt)
+        return;
+    const int len = min(FIN_RUN, cnt - r0);
+    unsigned long long *src = a.eps_list + (size_t)qb * a.eps_cap + r0;
+    for (int i = threadIdx.x; i < FIN_RUN; i += blockDim.x)
+        keys[i] = i < len ? src[i] : KNN_EMPTY_KEY;
+    __syncthreads();
+    for (int kk = 2; kk <= FIN_RUN; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < FIN_RUN; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & kk) == 0;
+                    const unsigned long long x = keys[i], y = keys[l];
+                    if ((x > y) == up) {
+                        keys[i] = y;
+                        keys[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < len; i += blockDim.x)
+        src[i] = keys[i];
+}
+
+// Number of keys taken from A among the first o keys of merge(A, B) (keys
+// unique): the smallest i with A[i] > B[o - i - 1].
+__device__ __forceinline__ int merge_corank(const unsigned long long *A, int la,
+                                            const unsigned long long *B, int lb, int o)
+{
+    int lo = max(0, o - lb), hi = min(o, la);
+    while (lo < hi) {
+        const int i = (lo + hi) >> 1;
+        if (A[i] < B[o - i - 1])
+            lo = i + 1;
+        else
+            hi = i;
+    }
+    return lo;
+}
+
+// One merge pass: sorted runs of width w (the last one shorter) are merged
+// pairwise from src into dst.  A thread writes FIN_MERGE_PER_THREAD
+// consecutive outputs, which lie in one pair of runs because 2w is a
+// multiple of that count.
+__global__ void __launch_bounds__(FIN_MERGE_THREADS)
+    fin_merge_kernel(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst,
+                     const int *__restrict__ eps_count, int cap, int w)
+{
+    const int qb = blockIdx.x;
+    const int cnt = fin_list_len(eps_count, cap, qb);
+    const int o0 = blockIdx.y * FIN_MERGE_TILE + threadIdx.x * FIN_MERGE_PER_THREAD;
+    if (o0 >= cnt)
+        return;
+    const unsigned long long *s = src + (size_t)qb * cap;
+    unsigned long long *d = dst + (size_t)qb * cap;
+    const int base = o0 / (2 * w) * (2 * w);
+    const int la = min(w, cnt - base);
+    const int lb = max(0, min(w, cnt - base - w));
+    const unsigned long long *A = s + base, *B = s + base + la;
+    int i = merge_corank(A, la, B, lb, o0 - base);
+    int j = o0 - base - i;
+    const int end = min(o0 + FIN_MERGE_PER_THREAD, cnt);
+    for (int o = o0; o < end; ++o) {
+        const unsigned long long x = i < la ? A[i] : KNN_EMPTY_KEY;
+        const unsigned long long y = j < lb ? B[j] : KNN_EMPTY_KEY;
+        if (x < y) {
+            d[o] = x;
+            ++i;
+        } else {
+            d[o] = y;
+            ++j;
+        }
+    }
+}
+
+// Mark the entries near eps for FP64 re-scoring; record the list length and
+// the values of the tail.
+__global__ void __launch_bounds__(FIN_THREADS) fin_big_mark_kernel(const FinArgs a)
+{
+    const int qb = blockIdx.x;
+    const int cnt = fin_list_len(a.eps_count, a.eps_cap, qb);
+    if (threadIdx.x == 0)
+        a.fin_valid[qb] = cnt;
+    const unsigned long long *keys = a.eps_list + (size_t)qb * a.eps_cap;
+    double *vals = a.fin_vals + (size_t)qb * a.fin_width;
+    const float w = a.rerank_rel, pivot = a.eps_int, lo = fin_tail_lo(a);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const float di = key_dist(keys[i]);
+        if (di < lo)
+            continue;
+        vals[i] = (double)di;
+        if (di >= pivot * (1.f - w) && di <= pivot * (1.f + w)) {
+            const int pos = atomicAdd(a.rer_count, 1);
+            if (pos < a.rer_cap)
+                a.rer_list[pos] = make_int2(qb, i);
+            else
+                atomicOr(a.status, KNN_DEV_CAPACITY);
+        }
+    }
+}
+
+// Output: the prefix below the tail is already in (value, id) order and is
+// written as it stands; the tail is re-ordered by (FP64 value where
+// re-scored, id) and cut at eps.
+__global__ void __launch_bounds__(FIN_THREADS) fin_big_out_kernel(const FinArgs a)
+{
+    extern __shared__ unsigned long long tkeys[];
+    double *tval = reinterpret_cast<double *>(tkeys + FIN_TAIL_CAP);
+    const int qb = blockIdx.x, tid = threadIdx.x;
+    const int cnt = a.fin_valid[qb];
+    const unsigned long long *keys = a.eps_list + (size_t)qb * a.eps_cap;
+    const double *vals = a.fin_vals + (size_t)qb * a.fin_width;
+    __shared__ int s_b1, s_kept;
+    if (tid == 0) {
+        const float lo = fin_tail_lo(a);
+        int l = 0, h = cnt;
+        while (l < h) {
+            const int mid = (l + h) >> 1;
+            if (key_dist(keys[mid]) < lo)
+                l = mid + 1;
+            else
+                h = mid;
+        }
+        s_b1 = l;
+    }
+    __syncthreads();
+    const int b1 = s_b1, tail = cnt - b1;
+    const int width = a.out_width;
+    int64_t *oid = a.out_ids + (size_t)qb * width;
+    float *odist = a.out_dist + (size_t)qb * width;
+    if (tail > FIN_TAIL_CAP) {
+        if (tid == 0)
+            atomicOr(a.status, KNN_DEV_BAD_SHAPE);
+        return;
+    }
+    for (int i = tid; i < b1; i += blockDim.x) {
+        const unsigned long long key = keys[i];
+        const float di = key_dist(key);
+        oid[i] = (int64_t)key_id(key);
+        odist[i] = a.kind == 0 ? di : (float)sqrt((double)di);
+    }
+    for (int i = tid; i < tail; i += blockDim.x) {
+        tkeys[i] = keys[b1 + i];
+        tval[i] = vals[b1 + i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 1; i < tail; ++i) {
+            const double v = tval[i];
+            const unsigned long long k = tkeys[i];
+            int j = i - 1;
+            while (j >= 0 && (tval[j] > v || (tval[j] == v && key_id(tkeys[j]) > key_id(k)))) {
+                tval[j + 1] = tval[j];
+                tkeys[j + 1] = tkeys[j];
+                --j;
+            }
+            tval[j + 1] = v;
+            tkeys[j + 1] = k;
+        }
+        int o = 0;
+        for (int i = 0; i < tail; ++i)
+            if (tval[i] <= (double)a.eps_int) {
+                tval[o] = tval[i];
+                tkeys[o] = tkeys[i];
+                ++o;
+            }
+        s_kept = o;
+    }
+    __syncthreads();
+    const int kept = b1 + s_kept;
+    for (int i = b1 + tid; i < width; i += blockDim.x) {
+        int64_t id = -1;
+        float dist = KNN_INF;
+        if (i < kept) {
+            id = (int64_t)key_id(tkeys[i - b1]);
+            dist = a.kind == 0 ? (float)tval[i - b1] : (float)sqrt(tval[i - b1]);
+        }
+        oid[i] = id;
+        odist[i] = dist;
+    }
+    if (tid == 0 && a.out_counts) {
+        const int raw = a.eps_count[qb];
+        a.out_counts[qb] = raw > a.eps_cap ? raw - (cnt - kept) : kept;
+        if (raw > a.eps_cap)
+            atomicOr(a.status, KNN_DEV_CAPACITY);
+    }
+}
+
+// Merge passes needed to sort a list of cap keys from runs of FIN_RUN.
+static int fin_merge_passes(int cap)
+{
+    int passes = 0;
+    for (int64_t w = FIN_RUN; w < cap; w *= 2)
+        ++passes;
+    return passes;
+}
+
 void fin_init_attributes()
 {
     cudaFuncSetAttribute(fin_rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     cudaFuncSetAttribute(fin_mark_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(fin_out_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(fin_big_out_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         FIN_TAIL_CAP * (sizeof(unsigned long long) + sizeof(double)));
 }
 
-void launch_finalize(const FinArgs &a, cudaStream_t st)
+int launch_finalize(const FinArgs &a, cudaStream_t st)
 {
+    const size_t smem_rer = (size_t)3 * (a.rer_row + 2) * sizeof(double);
+    const int rer_grid = a.rer_cap < 4096 ? a.rer_cap : 4096;
+    if (a.k == 0 && a.eps_cap > FIN_SMALL_CAP) {
+        int launches = 0;
+        // queries on x (up to 2^31 - 1), runs and tiles on y (<= 8192 at 2^24)
+        const dim3 runs(a.nq, (a.eps_cap + FIN_RUN - 1) / FIN_RUN);
+        fin_run_sort_kernel<<<runs, FIN_RUN_THREADS, 0, st>>>(a);
+        ++launches;
+        const int passes = fin_merge_passes(a.eps_cap);
+        const dim3 tiles(a.nq, (a.eps_cap + FIN_MERGE_TILE - 1) / FIN_MERGE_TILE);
+        unsigned long long *src = a.eps_list, *dst = a.eps_tmp;
+        for (int p = 0, w = FIN_RUN; p < passes; ++p, w *= 2) {
+            fin_merge_kernel<<<tiles, FIN_MERGE_THREADS, 0, st>>>(src, dst, a.eps_count,
+                                                                   a.eps_cap, w);
+            ++launches;
+            unsigned long long *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != a.eps_list)
+            cudaMemcpyAsync(a.eps_list, src, sizeof(unsigned long long) * a.nq * (size_t)a.eps_cap,
+                            cudaMemcpyDeviceToDevice, st);
+        fin_big_mark_kernel<<<a.nq, FIN_THREADS, 0, st>>>(a);
+        fin_rescore_kernel<<<rer_grid, fp64_threads(a.rer_row), smem_rer, st>>>(a);
+        fin_big_out_kernel<<<a.nq, FIN_THREADS,
+                             FIN_TAIL_CAP * (sizeof(unsigned long long) + sizeof(double)), st>>>(a);
+        return launches + 3;
+    }
     const size_t smem_mark = (size_t)a.sort_cap * sizeof(unsigned long long);
     const size_t smem_out = (size_t)a.sort_cap * (sizeof(unsigned long long) + sizeof(double));
     fin_mark_kernel<<<a.nq, FIN_THREADS, smem_mark, st>>>(a);
-    const size_t smem_rer = (size_t)3 * (a.rer_row + 2) * sizeof(double);
-    fin_rescore_kernel<<<a.rer_cap < 4096 ? a.rer_cap : 4096, fp64_threads(a.rer_row), smem_rer,
-                         st>>>(a);
+    fin_rescore_kernel<<<rer_grid, fp64_threads(a.rer_row), smem_rer, st>>>(a);
     fin_out_kernel<<<a.nq, FIN_THREADS, smem_out, st>>>(a);
+    return 3;
 }
 
 // ---------------------------------------------------------------------------

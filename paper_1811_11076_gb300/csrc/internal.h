@@ -70,6 +70,8 @@ struct LbArgs {
                                // kernel (nullable: no compaction)
     int compact;               // 0 automatic, 1 never, 2 whenever possible
     int k1, k2;                // compaction checkpoints in chunks (set by the launcher)
+    uint32_t fault_wait_spins; // tests only (KNN_FAULT_INJECT=wait): > 0 makes one thread
+                               // wait that many polls on a barrier nothing completes
 };
 // Floats of survivor-queue scratch one LB launch may need for nq queries.
 size_t lb_queue_floats(int n_sm, int nq);
@@ -183,6 +185,7 @@ struct FinArgs {
     int kslots;
     unsigned long long *slots;     // k-NN: [nq][kslots], ascending
     unsigned long long *eps_list;  // eps-NN: [nq][eps_cap] (sorted in place)
+    unsigned long long *eps_tmp;   // eps_cap > FIN_SMALL_CAP: [nq][eps_cap] merge buffer
     const int *eps_count;
     int eps_cap;
     int kind;
@@ -212,7 +215,13 @@ struct FinArgs {
     unsigned long long *stats;
     int *status;
 };
-void launch_finalize(const FinArgs &a, cudaStream_t st);
+// eps-NN lists up to this length are sorted in shared memory; longer ones
+// by a merge sort in global memory.
+constexpr int FIN_SMALL_CAP = 8192;
+// Largest eps-NN capacity per query.
+constexpr int64_t FIN_MAX_EPS_CAP = (int64_t)1 << 24;
+// Enqueues the finalisation; returns the number of kernels launched.
+int launch_finalize(const FinArgs &a, cudaStream_t st);
 void fin_init_attributes();
 
 // -- pair programs (no pruning) ----------------------------------------------

@@ -61,13 +61,6 @@ void launch_envelope(const EnvArgs &a, cudaStream_t st)
     envelope_kernel<<<grid, threads, 0, st>>>(a);
 }
 
-// Record which LB_Box kernel ran (bit of knn_stats.lb_kernels), once per launch.
-__device__ __forceinline__ void lb_mark(const LbArgs &a, unsigned long long bit)
-{
-    if (a.stats && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
-        atomicOr(a.stats + STAT_LB_KERNELS, bit);
-}
-
 // ---------------------------------------------------------------------------
 // TMA bulk copy global -> shared, completion tracked by an mbarrier
 
@@ -100,9 +93,9 @@ __device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_
 }
 
 // Bounded wait for phase 0 of the barrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait0(uint64_t *bar)
+__device__ __forceinline__ bool mbar_wait0(uint64_t *bar, uint32_t limit = KNN_SPIN_LIMIT)
 {
-    for (uint32_t it = 0; it < KNN_SPIN_LIMIT; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -117,6 +110,32 @@ __device__ __forceinline__ bool mbar_wait0(uint64_t *bar)
             __nanosleep(256);
     }
     return false;
+}
+
+// Fault injection for tests (a.fault_wait_spins > 0): one thread waits, with
+// that short limit, on a barrier that no arrival and no copy will ever
+// complete (nothing is in flight on it), gives up, and reports
+// KNN_DEV_TIMEOUT the way every bounded wait of the library does; the
+// kernel then carries on normally.
+__device__ __noinline__ void lb_fault_wait(const LbArgs &a)
+{
+    __shared__ __align__(8) uint64_t never;
+    mbar_init(&never, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait0(&never, a.fault_wait_spins))
+        atomicOr(a.status, KNN_DEV_TIMEOUT);
+}
+
+// Record which LB_Box kernel ran (bit of knn_stats.lb_kernels), once per
+// launch; the same thread runs the injected wait when one is requested.
+__device__ __forceinline__ void lb_mark(const LbArgs &a, unsigned long long bit)
+{
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        if (a.stats)
+            atomicOr(a.stats + STAT_LB_KERNELS, bit);
+        if (a.fault_wait_spins)
+            lb_fault_wait(a);
+    }
 }
 
 // One chunk of PPC whole points: accumulate the squared box distance of

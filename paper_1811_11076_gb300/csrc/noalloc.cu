@@ -83,7 +83,11 @@ NaPtrs carve(unsigned char *base)
     return p;
 }
 
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array on the current device, looked up once
+// per device ordinal and kept for the life of the process.  The address
+// belongs to the device's primary context: an application that destroys that
+// context (cudaDeviceReset) must not call knn_pairwise_noalloc on the device
+// afterwards, since the array may then live elsewhere.
 knn_status scratch_base(unsigned char **out)
 {
     static std::mutex mu;
@@ -245,12 +249,22 @@ extern "C" knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off,
     choose_dp_config(deff, band_radius(max_len, max_len, band), max_len, &P, &G);
     if (!P)
         return set_error(KNN_ERR_UNSUPPORTED, "band too wide for the compiled DP variants");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the call reads its status back and synchronises the stream, which a
+    // stream under capture does not allow: refuse before touching it
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess)
+        return cuda_error(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_error(KNN_ERR_INVALID,
+                         "knn_pairwise_noalloc cannot run while the stream is being captured");
     unsigned char *base = nullptr;
     knn_status s = scratch_base(&base);
     if (s)
         return s;
-    cudaStream_t st = (cudaStream_t)stream;
     const NaPtrs p = carve(base);
+    cudaGetLastError();  // an earlier, unrelated launch error is not this call's
     na_prepare_kernel<<<1, 1024, 0, st>>>(p, a_off, (int)n_a, b_off, (int)n_b, pa, pb,
                                           (int)n_pairs, max_len, deff);
     na_fill_kernel<<<512, 256, 0, st>>>(p, a, a_off, (int)n_a, b, b_off, (int)n_b, pa, pb,
@@ -280,11 +294,13 @@ extern "C" knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int occ = dp_max_blocks_per_sm(deff, P, distance);
-    launch_dp(x, deff, P, distance, nsm * (occ > 0 ? occ : 1), st);
+    if (!launch_dp(x, deff, P, distance, nsm * (occ > 0 ? occ : 1), st)) {
+        cudaStreamSynchronize(st);  // retire the two launches already enqueued
+        return set_error(KNN_ERR_UNSUPPORTED, "no DP kernel compiled for this d and shape");
+    }
     na_out_kernel<<<256, 256, 0, st>>>(p, (int)n_pairs, distance, out);
     int status = 0;
-    cudaError_t e = cudaMemcpyAsync(&status, &p.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost,
-                                    st);
+    e = cudaMemcpyAsync(&status, &p.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
     if (e == cudaSuccess)

@@ -50,7 +50,7 @@ struct Workspace {
     DevBuf env_lo, env_hi;
     DevBuf thr, slots, ub_slots;
     DevBuf items, item_lb;
-    DevBuf eps_list, eps_count;
+    DevBuf eps_list, eps_count, eps_tmp;
     DevBuf ctrl;                        // counters, status, stats
     DevBuf fin_valid, fin_vals, rer_list, rer_scratch;
     DevBuf out_ids, out_dist, out_counts;

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -43,6 +44,16 @@ struct Plan {
     int S = 0;                  // seeds per query
     DpChoice seed_dp{};
 };
+
+// Tests only: KNN_FAULT_INJECT=wait makes the LB_Box launches run one device
+// wait that cannot complete, with a limit of 4,096 polls (about a
+// millisecond), so that the bounded-wait path reports KNN_ERR_TIMEOUT
+// without faulting or hanging the GPU.  Read when the launch is enqueued.
+uint32_t fault_wait_spins()
+{
+    const char *f = getenv("KNN_FAULT_INJECT");
+    return f && !strcmp(f, "wait") ? 4096u : 0u;
+}
 
 knn_status grow(Workspace &ws, DevBuf &b, size_t bytes)
 {
@@ -148,9 +159,9 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
     pl.eps_cap = p.k > 0 ? 0 : p.eps_capacity;
     pl.kslots = p.k > 0 ? p.k + std::max(8, p.k / 2) : 0;
     pl.width = p.k > 0 ? p.k : (int)p.eps_capacity;
-    pl.sort_cap = next_pow2i(std::max(pl.kslots, (int)pl.eps_cap));
-    if (pl.sort_cap > 8192)
-        return set_error(KNN_ERR_UNSUPPORTED, "eps_capacity above 8192");
+    if (pl.eps_cap > FIN_MAX_EPS_CAP)
+        return set_error(KNN_ERR_UNSUPPORTED, "eps_capacity above 2^24");
+    pl.sort_cap = next_pow2i(std::max(pl.kslots, (int)std::min<int64_t>(pl.eps_cap, FIN_SMALL_CAP)));
     pl.mg = margins_for(p.distance, pl.max_m + db->max_len, db->deff);
     pl.eps_int = p.distance == KNN_DK ? p.eps * p.eps : p.eps;
     pl.rer_row = 2 * band_radius(pl.max_m, db->max_len, p.band) + 1;
@@ -194,6 +205,8 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(items, sizeof(int2) * pl.items_cap);
     G_(item_lb, sizeof(float) * pl.items_cap);
     G_(eps_list, sizeof(unsigned long long) * nq * std::max<int64_t>(pl.eps_cap, 1));
+    if (pl.eps_cap > FIN_SMALL_CAP)
+        G_(eps_tmp, sizeof(unsigned long long) * nq * pl.eps_cap);
     G_(eps_count, sizeof(int) * nq);
     G_(ctrl, sizeof(Ctrl));
     G_(fin_valid, sizeof(int) * nq);
@@ -259,8 +272,43 @@ DpArgs dp_args(knn_db *db, const Plan &pl, const knn_params &p, const int2 *item
 // the LB_Box stream, [3] after seed selection and seed programs, [4] after the
 // survivor filter, [5] after the DP, [6] after finalise.
 struct StageEvents {
-    cudaEvent_t ev[7];
-    cudaEvent_t seg[MAX_SEG + 1];
+    cudaEvent_t ev[7] = {};
+    cudaEvent_t seg[MAX_SEG + 1] = {};
+    bool live = false;
+    void create()
+    {
+        for (auto &e : ev)
+            cudaEventCreate(&e);
+        for (auto &e : seg)
+            cudaEventCreate(&e);
+        live = true;
+    }
+    ~StageEvents()
+    {
+        if (!live)
+            return;
+        for (auto &e : ev)
+            cudaEventDestroy(e);
+        for (auto &e : seg)
+            cudaEventDestroy(e);
+    }
+};
+
+// The call's two timing events, destroyed on every return path.
+struct CallEvents {
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    CallEvents()
+    {
+        cudaEventCreate(&ev0);
+        cudaEventCreate(&ev1);
+    }
+    ~CallEvents()
+    {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+    }
+    CallEvents(const CallEvents &) = delete;
+    CallEvents &operator=(const CallEvents &) = delete;
 };
 
 // All launches of one batch; capturable (no host synchronisation, no
@@ -413,6 +461,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         }
         l.stats = stats;
         l.status = &ctrl->status;
+        l.fault_wait_spins = fault_wait_spins();
         launch_lb(l, db->deff, kind, db->n_sm, st);
         launches += 2;
     }
@@ -496,6 +545,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     f.kslots = pl.kslots;
     f.slots = ws.slots.as<unsigned long long>();
     f.eps_list = ws.eps_list.as<unsigned long long>();
+    f.eps_tmp = pl.eps_cap > FIN_SMALL_CAP ? ws.eps_tmp.as<unsigned long long>() : nullptr;
     f.eps_count = ws.eps_count.as<int>();
     f.eps_cap = (int)pl.eps_cap;
     f.kind = kind;
@@ -523,8 +573,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     f.out_width = pl.width;
     f.stats = stats;
     f.status = &ctrl->status;
-    launch_finalize(f, st);
-    launches += 3;
+    launches += launch_finalize(f, st);
     if (sev)
         cudaEventRecord(sev->ev[6], st);
     return launches;
@@ -603,10 +652,8 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
 
     Workspace &ws = db->ws;
     knn_status s;
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventRecord(ev0, st);
+    CallEvents cev;
+    cudaEventRecord(cev.ev0, st);
 
     // queries and their point offsets on the device, relative to hq[0]
     const int64_t qpts = hq[n_queries] - hq[0];
@@ -656,12 +703,8 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
     double stage_ms[4] = {0, 0, 0, 0};
     const bool profile = p.profile != 0 && !graph;
     StageEvents sev;
-    if (profile) {
-        for (auto &ev : sev.ev)
-            cudaEventCreate(&ev);
-        for (auto &ev : sev.seg)
-            cudaEventCreate(&ev);
-    }
+    if (profile)
+        sev.create();
     db->seg_ms.clear();
     db->seg_first_bucket.clear();
     for (int q0 = 0; q0 < n_queries; q0 += batch) {
@@ -770,7 +813,7 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         if (e != cudaSuccess)
             return cuda_error(e, "launch");
     }
-    cudaEventRecord(ev1, st);
+    cudaEventRecord(cev.ev1, st);
     Ctrl hc;
     cudaError_t e = cudaMemcpyAsync(&hc, ws.ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
@@ -778,15 +821,7 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
     if (e != cudaSuccess)
         return cuda_error(e, "scan");
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    if (profile) {
-        for (auto &ev : sev.ev)
-            cudaEventDestroy(ev);
-        for (auto &ev : sev.seg)
-            cudaEventDestroy(ev);
-    }
+    cudaEventElapsedTime(&ms, cev.ev0, cev.ev1);
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->pairs = (int64_t)hc.stats[STAT_PAIRS];

@@ -230,6 +230,64 @@ def test_eps_nn(kw, kind):
         np.testing.assert_allclose(dist[q, :c], e_dist[q, :c], rtol=DTW_TOL if kind == 0 else DK_TOL)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_eps_nn_large_capacity(kw, kind):
+    """eps-NN with more than 8,192 results per query (global-memory merge
+    sort of the result lists).  The result set and counts equal the oracle's;
+    each reported distance agrees with the oracle's for that id; rows are in
+    the order of the reported values, and no two entries are inverted by more
+    than the tolerance of the exact values."""
+    import torch
+    w = make_workload(n_series=24_000, n_queries=3, d=2, length=48, n_classes=4, seed=17)
+    band = f32(0.1)
+    tol = DTW_TOL if kind == 0 else DK_TOL
+    # eps at the median distance of query 0: about half the database per query
+    sample = oracle.knn(w.db[: w.db_off[2001]], w.db_off[:2001], w.query(0), [0, 48],
+                        band=band, kind=kind, k=2000)[1]
+    eps = f32(np.median(sample))
+    cap = 24_000
+    e_ids, e_dist, e_cnt = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=band, kind=kind, k=0,
+                                      eps=eps, cap=cap)
+    assert e_cnt.min() > 8192
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    ids, dist, cnt = db.scan(cuda(w.q), w.q_off, k=0, eps=eps, eps_capacity=cap, band=0.1,
+                             distance=kind)
+    ids, dist, cnt = ids.cpu().numpy(), dist.cpu().numpy(), cnt.cpu().numpy()
+    np.testing.assert_array_equal(cnt, e_cnt)
+    for q in range(3):
+        c = int(cnt[q])
+        exact = dict(zip(e_ids[q, :c].tolist(), e_dist[q, :c].tolist()))
+        got = ids[q, :c].tolist()
+        assert set(got) == set(exact)
+        ex = np.array([exact[i] for i in got])
+        np.testing.assert_allclose(dist[q, :c], ex, rtol=tol, atol=1e-30)
+        # reported distances never decrease; exact values are inverted by no
+        # more than the tolerance (DK: distinct squares may round to one float)
+        assert np.all(np.diff(dist[q, :c]) >= 0)
+        assert np.all(ex[1:] >= ex[:-1] * (1 - 2 * tol))
+        assert np.all(ids[q, c:] == -1) and np.all(np.isinf(dist[q, c:]))
+    # capacity overflow on the same path: true counts and valid entries
+    small = 9000
+    o = (torch.empty((3, small), dtype=torch.int64, device="cuda"),
+         torch.empty((3, small), dtype=torch.float32, device="cuda"),
+         torch.empty(3, dtype=torch.int64, device="cuda"))
+    with pytest.raises(kw.KnnError) as e:
+        db.scan(cuda(w.q), w.q_off, k=0, eps=eps, eps_capacity=small, band=0.1, distance=kind,
+                out=o)
+    assert e.value.status == 5
+    db.close()
+    # counts of overflowing rows bound the true sizes from above, exceeding
+    # them only by results within the FP32 band of eps that were not stored
+    band_cnt = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=band, kind=kind, k=0,
+                          eps=eps * (1 + 1e-4), cap=cap)[2]
+    got_cnt = o[2].cpu().numpy()
+    assert np.all(got_cnt >= e_cnt) and np.all(got_cnt <= band_cnt)
+    oi = o[0].cpu().numpy()
+    for q in range(3):
+        exact = set(e_ids[q, : int(e_cnt[q])].tolist())
+        assert set(x for x in oi[q].tolist() if x >= 0) <= exact
+
+
 def test_seed_modes_and_graph_give_identical_results(kw):
     w = make_workload(n_series=2500, n_queries=8, d=3, length=96, n_classes=10, seed=8)
     for kind in (0, 1):

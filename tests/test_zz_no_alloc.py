@@ -37,28 +37,64 @@ def _call(kw, a, a_off, b, b_off, pa, pb, d, band, max_len, kind, out):
 
 @pytest.mark.parametrize("kind", [0, 1])
 def test_noalloc_matches_allocating_pairwise(kw, kind):
+    """Calls in a row (d = 3, 5, 12 with its zero-padded coordinates, 1): each
+    result equals knn_pairwise's and the FP64 oracle's within the tolerance,
+    and once the first call has loaded the library's array no call changes
+    the device's free memory."""
     import torch
+    import oracle
     tol = 1e-5 if kind == 0 else 1e-6
-    for call, (d, seed) in enumerate([(3, 1), (5, 2)]):      # two calls in a row
+    free_before = []
+    for call, (d, seed) in enumerate([(3, 1), (5, 2), (12, 3), (1, 4)]):
         wa = make_workload(n_series=150, n_queries=0, d=d, length_range=(30, 120), n_classes=4,
                            seed=100 + seed)
         wb = make_workload(n_series=220, n_queries=0, d=d, length_range=(30, 120), n_classes=4,
                            seed=200 + seed)
         rng = np.random.default_rng(seed)
         n = 2000
-        pa = torch.from_numpy(rng.integers(0, 150, n)).cuda()
-        pb = torch.from_numpy(rng.integers(0, 220, n)).cuda()
+        pa_h, pb_h = rng.integers(0, 150, n), rng.integers(0, 220, n)
+        pa, pb = torch.from_numpy(pa_h).cuda(), torch.from_numpy(pb_h).cuda()
         a, a_off = torch.from_numpy(wa.db).cuda(), torch.from_numpy(wa.db_off).cuda()
         b, b_off = torch.from_numpy(wb.db).cuda(), torch.from_numpy(wb.db_off).cuda()
         band = 0.1
         ref, _ = kw.pairwise(a, a_off, b, b_off, pa, pb, band=band, distance=kind)
         out = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = _call(kw, a, a_off, b, b_off, pa, pb, d, band, 120, kind, out)
         assert st == 0, kw.lib().knn_last_error()
+        torch.cuda.synchronize()
+        free_before.append((free0, torch.cuda.mem_get_info()[0]))
         got, exp = out.cpu().numpy(), ref.cpu().numpy()
         fin = np.isfinite(exp)
         assert np.array_equal(np.isinf(got), ~fin), call
         np.testing.assert_allclose(got[fin], exp[fin], rtol=tol, atol=0)
+        orc = oracle.pairwise(wa.db, wa.db_off, wb.db, wb.db_off, pa_h, pb_h,
+                              band=float(np.float32(band)), kind=kind)
+        assert np.array_equal(np.isfinite(orc), fin), call
+        np.testing.assert_allclose(got[fin], orc[fin], rtol=tol, atol=0)
+    # no device memory is taken by any call after the first
+    for f0, f1 in free_before[1:]:
+        assert f0 == f1
+
+
+def test_noalloc_refuses_a_stream_under_capture(kw):
+    import torch
+    w = make_workload(n_series=8, n_queries=0, d=2, length=30, n_classes=2, seed=7)
+    a, a_off = torch.from_numpy(w.db).cuda(), torch.from_numpy(w.db_off).cuda()
+    idx = torch.zeros(4, dtype=torch.int64, device="cuda")
+    out = torch.empty(4, dtype=torch.float32, device="cuda")
+    assert _call(kw, a, a_off, a, a_off, idx, idx, 2, 0.1, 30, 0, out) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        st = _call(kw, a, a_off, a, a_off, idx, idx, 2, 0.1, 30, 0, out)
+        g.capture_end()
+    torch.cuda.synchronize()
+    assert st == 1 and b"captured" in kw.lib().knn_last_error()
+    assert _call(kw, a, a_off, a, a_off, idx, idx, 2, 0.1, 30, 0, out) == 0
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(kw):
