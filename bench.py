@@ -430,6 +430,9 @@ def run_gpu(args):
             "dp_calls_per_query": agg["dp_calls"] / (nq * len(sts)),
             "dp_abandoned_frac": agg["dp_abandoned"] / max(agg["dp_calls"], 1),
             "lb_pruned_frac": (agg["lb_pruned"] + agg["lb_pruned_late"]) / max(agg["pairs"], 1),
+            "coarse_pruned_frac": agg["lb_coarse_pruned"] / max(agg["pairs"], 1),
+            "lb_points_per_query": agg["lb_points"] / (nq * len(sts)),
+            "coarse_segments_per_query": agg["lb_segments"] / (nq * len(sts)),
             "dp_cells_per_query": agg["dp_cells"] / (nq * len(sts)),
             "seed_cells_per_query": agg["seed_cells"] / (nq * len(sts)),
             "reranked": agg["reranked"] // len(sts),
@@ -451,7 +454,8 @@ def run_gpu(args):
         for k_ in stage:
             stage[k_] += s[f"ms_{k_}"]
         dp_ops += s["dp_cells"] * (2 * D + 3)
-        lb_ops += s["lb_points"] * (4 * D + (1 if kind == kw.DK else 0))
+        # exact LB_Box points and coarse segments cost the same per element
+        lb_ops += (s["lb_points"] + s["lb_segments"]) * (4 * D + (1 if kind == kw.DK else 0))
     clocks = clk.summary()
     share = {k_: v / max(sum(stage.values()), 1e-12) for k_, v in stage.items()}
 
@@ -471,8 +475,9 @@ def run_gpu(args):
     lb_bits = 0
     for s in list(prof.values()) + [s for _, s in collected]:
         lb_bits |= int(s.get("lb_kernels", 0))
-    lb_name = "+".join(n_ for b_, n_ in ((1, "lb_kernel"), (2, "lb_multi_kernel"),
-                                         (4, "lb_win_kernel"), (8, "lb_compact_kernel"))
+    lb_name = "+".join(n_ for b_, n_ in ((16, "lb_coarse_kernel+lb_pair_kernel"), (1, "lb_kernel"),
+                                         (2, "lb_multi_kernel"), (4, "lb_win_kernel"),
+                                         (8, "lb_compact_kernel"))
                        if lb_bits & b_) or "lb_multi_kernel"
     stage_roofs = {"lb": alu_roof(lb_name, lb_ops, stage["lb"]),
                    "dp": alu_roof("dp_kernel", dp_ops, stage["dp"])}
@@ -517,9 +522,11 @@ def run_gpu(args):
         modes = [("plain_lb", kw.SEED_LB, None), ("greedy", kw.SEED_GREEDY, None)]
         if cmp_db is not None:
             modes.append(("learned_untrained", kw.SEED_LEARNED, cmp_db))
+        modes.append(("no_coarse_stage", seed_mode, None))
         for kind in kinds:
             for mname, mode, other in modes:
                 h = other or dbs[kind]
+                h.set_lb_cascade(kind, 1 if mname == "no_coarse_stage" else 0)
                 if other is not None:
                     h.set_lb_tile(kind, *dbs[kind].get_lb_tile(kind))
                     if LENGTH:
@@ -541,6 +548,7 @@ def run_gpu(args):
                 cms = c0.elapsed_time(c1)
                 same = bool(torch.equal(o[0], headline[kind][0]) and
                             torch.equal(o[1], headline[kind][1]))
+                dbs[kind].set_lb_cascade(kind, 0)
                 comparators[f"{kname[kind]}/{mname}"] = {
                     "queries_per_s": nq * n_cmp / (cms / 1000.0), "scans_timed": n_cmp,
                     "identical_results": same,

@@ -132,7 +132,10 @@ typedef struct {
     double ms_finalize;      /* profile = 1: FP64 re-scoring and output          */
     int64_t lb_kernels;      /* LB_Box kernels that ran, bit mask: 1 one query per
                                 pass, 2 whole envelopes, 4 windowed envelopes,
-                                8 whole envelopes with compaction              */
+                                8 whole envelopes with compaction, 16 the
+                                coarse first stage (segment boxes)             */
+    int64_t lb_coarse_pruned; /* pairs pruned by the coarse first stage          */
+    int64_t lb_segments;     /* (query, series segment) pairs it bounded         */
 } knn_stats;
 
 typedef struct knn_db knn_db;
@@ -238,6 +241,23 @@ KNN_API knn_status knn_set_lb_tile(knn_db *db, int32_t distance, int32_t qtile,
 KNN_API knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qtile,
                                    int32_t *window_chunks, int32_t *compaction);
 
+/* Coarse first stage of the LB_Box cascade (Section 3, Eq. 1 over segment
+ * boxes).  The points of a series are grouped into segments of W consecutive
+ * points (W = 16 for d >= 8, else 4; partial last segments left out), B_s is
+ * the smallest box holding the query envelope's boxes B_j of segment s, and
+ *     LB_seg = sum_s W * dist(mean of the segment's points, B_s)^2
+ * (form 0; form 1: the max over segments of dist^2) is at most LB_Box, by
+ * convexity of the squared distance to a box.  The segment means are built
+ * with the database.  In the filtering scan, pairs the coarse bound prunes
+ * never reach LB_Box; the others get the exact LB_Box, and only its
+ * survivors reach the dynamic program.  coarse = 0 (automatic): used for
+ * every bucket whose shortest series has at least 4 segments; 1: never.
+ * Results never depend on it.  knn_get_lb_cascade also returns W
+ * (segment_width nullable).  KNN_ERR_INVALID for other values. */
+KNN_API knn_status knn_set_lb_cascade(knn_db *db, int32_t distance, int32_t coarse);
+KNN_API knn_status knn_get_lb_cascade(knn_db *db, int32_t distance, int32_t *coarse,
+                                      int32_t *segment_width);
+
 /* ---------------------------------------------------------------------- */
 /* Components (each is one step of the scan, exposed for verification and  */
 /* for callers who build their own pipelines).  All pointers device memory. */
@@ -255,6 +275,13 @@ KNN_API knn_status knn_envelope(const float *t, int64_t n, int32_t d, int64_t r,
  * DTW); form 1: max over points (bounds DK^2).  out_lb[n_series] in the
  * caller's series order; band-infeasible series get +inf. */
 KNN_API knn_status knn_lb_box(knn_db *db, const float *query, int64_t m, float band,
+                              int32_t form, float *out_lb, void *stream);
+
+/* The coarse bound LB_seg of every database series against `query` (see
+ * knn_set_lb_cascade; the same units as knn_lb_box, form 0 or 1), a lower
+ * bound of knn_lb_box's value.  out_lb[n_series] in the caller's series
+ * order; band-infeasible series get +inf. */
+KNN_API knn_status knn_lb_seg(knn_db *db, const float *query, int64_t m, float band,
                               int32_t form, float *out_lb, void *stream);
 
 /* Greedy upper bound of every database series (Section 4.1, Algorithm 1,

@@ -59,6 +59,9 @@ def lib():
             L.orc_lb_keogh_1d.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int64]
             L.orc_lb_box.restype = C.c_double
             L.orc_lb_box.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int64, C.c_int]
+            L.orc_lb_seg.restype = C.c_double
+            L.orc_lb_seg.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int64, C.c_int64,
+                                     C.c_int]
             L.orc_lb_sigma_min.restype = C.c_double
             L.orc_lb_sigma_min.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int64]
             L.orc_greedy.restype = C.c_double
@@ -147,6 +150,15 @@ def lb_box(s, t, r: int, form: int = 0) -> float:
     """LB_Box (Section 3, Eq. 1): form 0 sums, form 1 takes the max (squared)."""
     s, t, m, n, d = _pair_args(s, t)
     return lib().orc_lb_box(_p(s), m, _p(t), n, d, r, form)
+
+
+def lb_seg(s, t, r: int, W: int, form: int = 0) -> float:
+    """LB_Box over segment boxes of W points (the cascade's coarse stage,
+    Section 3 Eq. 1 on coarsened boxes): W * squared distance of each whole
+    segment's mean of s to the box holding its envelope boxes, summed (form
+    0) or the max of the squared distances (form 1)."""
+    s, t, m, n, d = _pair_args(s, t)
+    return lib().orc_lb_seg(_p(s), m, _p(t), n, d, r, W, form)
 
 
 def lb_sigma_min(s, t, r: int) -> float:

@@ -232,6 +232,50 @@ double orc_lb_box(const double *s, int64_t m, const double *t, int64_t n, int d,
     return acc;
 }
 
+/* LB_Box over segment boxes (the coarse first stage of the cascade; Eq. 1 of
+ * Section 3 applied to coarsened boxes).  The points of s are grouped into
+ * segments of W consecutive points (a partial last segment is left out); the
+ * box of segment g is the smallest box holding the envelope boxes B_i of t
+ * (window |p - i| <= r) of its points, and the bound is
+ *   form 0: sum_g W * ||mean_g(s) - clamp(mean_g(s), box_g)||^2
+ *   form 1: max_g     ||mean_g(s) - clamp(mean_g(s), box_g)||^2.
+ * An empty window (no point of t within r) makes the pair infeasible: +inf. */
+double orc_lb_seg(const double *s, int64_t m, const double *t, int64_t n, int d, int64_t r,
+                  int64_t W, int form)
+{
+    double *l = malloc(sizeof(double) * (size_t)(m * d));
+    double *u = malloc(sizeof(double) * (size_t)(m * d));
+    orc_envelope(t, n, d, r, m, l, u);
+    double acc = 0.0;
+    for (int64_t g = 0; g + W <= m; g += W) {
+        double box = 0.0;
+        for (int j = 0; j < d; ++j) {
+            double lo = ORC_INF, hi = -ORC_INF, mean = 0.0;
+            for (int64_t i = g; i < g + W; ++i) {
+                if (l[i * d + j] < lo)
+                    lo = l[i * d + j];
+                if (u[i * d + j] > hi)
+                    hi = u[i * d + j];
+                mean += s[i * d + j];
+            }
+            mean /= (double)W;
+            if (lo > hi) {
+                box = ORC_INF;
+                break;
+            }
+            double e = dist_interval(mean, lo, hi);
+            box += e * e;
+        }
+        if (form == 0)
+            acc += (double)W * box;
+        else if (box > acc)
+            acc = box;
+    }
+    free(l);
+    free(u);
+    return acc;
+}
+
 /* LB_Sigma-min (Section 3): sum_i min_{|l|<=r} d(s_i, t_{i+l})^2. */
 double orc_lb_sigma_min(const double *s, int64_t m, const double *t, int64_t n, int d,
                         int64_t r)

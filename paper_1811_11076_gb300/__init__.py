@@ -38,7 +38,8 @@ STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA"
 EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_scan_simple",
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
-           "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_subseq", "knn_subseq_greedy", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
+           "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_set_lb_cascade",
+           "knn_get_lb_cascade", "knn_lb_seg", "knn_subseq", "knn_subseq_greedy", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
            "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach",
            "knn_encoder_params", "knn_encoder_loss_grad", "knn_encoder_save", "knn_encoder_load")
 
@@ -75,7 +76,8 @@ class Stats(C.Structure):
                 ("dp_calls", C.c_int64), ("dp_abandoned", C.c_int64), ("dp_cells", C.c_int64),
                 ("reranked", C.c_int64), ("lb_points", C.c_int64), ("launches", C.c_int64), ("ms_total", C.c_double),
                 ("ms_seed", C.c_double), ("ms_lb", C.c_double), ("ms_dp", C.c_double),
-                ("ms_finalize", C.c_double), ("lb_kernels", C.c_int64)]
+                ("ms_finalize", C.c_double), ("lb_kernels", C.c_int64),
+                ("lb_coarse_pruned", C.c_int64), ("lb_segments", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -106,6 +108,9 @@ def lib() -> C.CDLL:
     L.knn_envelope.argtypes = [vp, C.c_int64, C.c_int32, C.c_int64, C.c_int64, vp, vp, vp]
     L.knn_lb_box.argtypes = [vp, vp, C.c_int64, C.c_float, C.c_int32, vp, vp]
     L.knn_greedy_ub.argtypes = [vp, vp, C.c_int64, C.c_float, C.c_int32, vp, vp]
+    L.knn_lb_seg.argtypes = [vp, vp, C.c_int64, C.c_float, C.c_int32, vp, vp]
+    L.knn_set_lb_cascade.argtypes = [vp, C.c_int32, C.c_int32]
+    L.knn_get_lb_cascade.argtypes = [vp, C.c_int32] + [C.POINTER(C.c_int32)] * 2
     L.knn_pairwise.argtypes = [vp, vp, vp, vp, vp, vp, C.c_int64, C.c_int32, C.c_float,
                                C.c_int32, vp, vp, vp]
     L.knn_autotune.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(Params), C.c_char_p, vp]
@@ -278,6 +283,25 @@ class KnnDB:
         q, w, c = C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().knn_get_lb_tile(self._h, distance, C.byref(q), C.byref(w), C.byref(c)))
         return q.value, w.value, c.value
+
+    def set_lb_cascade(self, distance: int, coarse: int = 0):
+        """Coarse first LB stage (segment boxes): 0 automatic, 1 never."""
+        _check(lib().knn_set_lb_cascade(self._h, distance, coarse))
+
+    def get_lb_cascade(self, distance: int):
+        """(setting, segment width W)."""
+        c, w = C.c_int32(), C.c_int32()
+        _check(lib().knn_get_lb_cascade(self._h, distance, C.byref(c), C.byref(w)))
+        return c.value, w.value
+
+    def lb_seg(self, query, band: float, form: int = 0, stream=None):
+        """Coarse (segment box) bound of every series (device tensor out)."""
+        import torch
+        query = _f32(query)
+        out = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        _check(lib().knn_lb_seg(self._h, _ptr(query), int(query.shape[0]), band, form, _ptr(out),
+                                _stream(stream)))
+        return out
 
     def get_dp_shape(self, distance: int, r: int, n: int):
         P, G = C.c_int32(), C.c_int32()

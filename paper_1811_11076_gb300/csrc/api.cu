@@ -280,6 +280,7 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
     std::call_once(attr_once, [] {
         lb_init_attributes();
         fin_init_attributes();
+        lbc_init_attributes();
     });
     auto db = new knn_db();
     db->d = d;
@@ -379,13 +380,48 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
     }
     launch_repack(src, (const int64_t *)off_stage.p, (const int *)db->id.p, N, d, deff,
                   (const int64_t *)db->off.p, (float *)db->data.p, st, true);
-    e = cudaStreamSynchronize(st);
+
+    // coarse first stage of the LB_Box cascade: scaled segment means of every
+    // series (full segments only) and the largest coordinate magnitude
+    const int W = coarse_width(deff);
+    std::vector<int64_t> sg_off(N), sg_end(N);
+    int64_t sg_total = 0;
+    for (int c = 0; c < N; ++c) {
+        const int nseg = db->h_len[c] / W;
+        sg_off[c] = sg_total;
+        sg_total += (int64_t)((nseg + PPC - 1) / PPC) * CH;
+        sg_end[c] = sg_total;
+    }
+    DevBuf sg_end_dev;
+    if ((s = db->sg.ensure(sizeof(float) * std::max<int64_t>(sg_total, 4))) ||
+        (s = db->sg_off.ensure(sizeof(int64_t) * N)) ||
+        (s = sg_end_dev.ensure(sizeof(int64_t) * N))) {
+        delete db;
+        return s;
+    }
+    cpy(db->sg_off.p, sg_off.data(), sizeof(int64_t) * N);
+    cpy(sg_end_dev.p, sg_end.data(), sizeof(int64_t) * N);
+    if (e != cudaSuccess) {
+        delete db;
+        return cuda_error(e, "copy segment offsets");
+    }
+    launch_seg_means((const float *)db->data.p, (const int64_t *)db->off.p,
+                     (const int *)db->len.p, N, deff, W, (const int64_t *)db->sg_off.p,
+                     (const int64_t *)sg_end_dev.p, (float *)db->sg.p, st);
+    unsigned int *amax = reinterpret_cast<unsigned int *>((char *)db->ws.ctrl.p + 256);
+    launch_absmax(src + hoff[0] * d, (npts - hoff[0]) * d, amax, st);
+    unsigned int amax_bits = 0;
+    e = cudaMemcpyAsync(&amax_bits, amax, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
     if (e == cudaSuccess)
         e = cudaGetLastError();
     if (e != cudaSuccess) {
         delete db;
         return cuda_error(e, "repack database");
     }
+    memcpy(&db->absmax, &amax_bits, sizeof(float));
+    db->seg_w = W;
     *out = db;
     return KNN_OK;
 }

@@ -305,6 +305,31 @@ extern "C" knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qti
     return KNN_OK;
 }
 
+extern "C" knn_status knn_set_lb_cascade(knn_db *db, int32_t distance, int32_t coarse)
+{
+    if (!db)
+        return set_error(KNN_ERR_INVALID, "db is NULL");
+    if (distance != KNN_DTW && distance != KNN_DK)
+        return set_error(KNN_ERR_INVALID, "distance must be KNN_DTW or KNN_DK");
+    if (coarse != 0 && coarse != 1)
+        return set_error(KNN_ERR_INVALID, "coarse must be 0 (automatic) or 1 (never)");
+    db->lb_coarse[distance] = coarse;
+    return KNN_OK;
+}
+
+extern "C" knn_status knn_get_lb_cascade(knn_db *db, int32_t distance, int32_t *coarse,
+                                         int32_t *segment_width)
+{
+    if (!db || !coarse)
+        return set_error(KNN_ERR_INVALID, "NULL argument");
+    if (distance != KNN_DTW && distance != KNN_DK)
+        return set_error(KNN_ERR_INVALID, "distance must be KNN_DTW or KNN_DK");
+    *coarse = db->lb_coarse[distance];
+    if (segment_width)
+        *segment_width = db->seg_w;
+    return KNN_OK;
+}
+
 extern "C" int32_t knn_dp_shapes(int32_t d, int32_t *P_list, int32_t cap)
 {
     const int deff = deff_for(d);

@@ -107,9 +107,12 @@ extern "C" knn_status knn_envelope(const float *t, int64_t n, int32_t d, int64_t
     return KNN_OK;
 }
 
+// mode 0: LB_Box (Eq. 1); 1: greedy bound (Algorithm 1); 2: coarse bound
+// over segment boxes (the cascade's first stage).
 static knn_status bound_common(knn_db *db, const float *query, int64_t m, float band, int32_t form,
-                               float *out, void *stream, bool greedy)
+                               float *out, void *stream, int mode)
 {
+    const bool greedy = mode == 1;
     if (!db || !query || !out)
         return set_error(KNN_ERR_INVALID, "NULL argument");
     if (m < 1 || !(band > 0.f) || (form != 0 && form != 1))
@@ -166,6 +169,56 @@ static knn_status bound_common(knn_db *db, const float *query, int64_t m, float 
             e.lo = ws.env_lo.as<float>();
             e.hi = ws.env_hi.as<float>();
             launch_envelope(e, st);
+            if (mode == 2) {
+                const int W = db->seg_w, nseg = b.n_hi / W;
+                const int box_floats = std::max(4, (nseg + PPC - 1) / PPC * CH);
+                if ((s = ws.sbox_lo.ensure(sizeof(float) * box_floats)) ||
+                    (s = ws.sbox_hi.ensure(sizeof(float) * box_floats)))
+                    return s;
+                if (!coarse_qtile(box_floats))
+                    return set_error(KNN_ERR_UNSUPPORTED, "segment boxes larger than shared memory");
+                SegBoxArgs sb{};
+                sb.env_lo = ws.env_lo.as<float>();
+                sb.env_hi = ws.env_hi.as<float>();
+                sb.env_stride = env;
+                sb.nq = 1;
+                sb.d = db->deff;
+                sb.W = W;
+                sb.nseg = nseg;
+                sb.scale = W == 16 ? 4.f : 2.f;
+                sb.box_lo = ws.sbox_lo.as<float>();
+                sb.box_hi = ws.sbox_hi.as<float>();
+                sb.box_stride = box_floats;
+                sb.box_floats = box_floats;
+                launch_seg_boxes(sb, st);
+                CoarseArgs c{};
+                c.sg = db->sg.as<float>();
+                c.sg_off = db->sg_off.as<int64_t>();
+                c.db_len = db->len.as<int>();
+                c.W = W;
+                c.inv_w = 1.f / (float)W;
+                c.c_begin = b.c_begin;
+                c.c_end = b.c_end;
+                c.n_lo = b.n_lo;
+                c.n_hi = b.n_hi;
+                c.q_len = ws.q_len.as<int>();
+                c.nq = 1;
+                c.band = band;
+                c.box_lo = ws.sbox_lo.as<float>();
+                c.box_hi = ws.sbox_hi.as<float>();
+                c.box_stride = box_floats;
+                c.box_floats = box_floats;
+                c.nseg_hi = nseg;
+                c.M = db->absmax;
+                c.thr = ws.thr.as<float>();
+                c.mu_prune = 1.f;
+                c.out_lb = tmp;
+                c.out_lb_stride = db->N;
+                c.stats = ctrl->stats;
+                c.status = &ctrl->status;
+                launch_lb_coarse(c, db->deff, form, db->n_sm, st);
+                continue;
+            }
             LbArgs l{};
             l.db = db->data.as<float>();
             l.db_off = db->off.as<int64_t>();
@@ -197,7 +250,7 @@ static knn_status bound_common(knn_db *db, const float *query, int64_t m, float 
     if (e == cudaSuccess)
         e = cudaGetLastError();
     if (e != cudaSuccess)
-        return cuda_error(e, greedy ? "greedy bound" : "lb_box");
+        return cuda_error(e, greedy ? "greedy bound" : mode == 2 ? "lb_seg" : "lb_box");
     int status = 0;
     cudaMemcpy(&status, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost);
     if (status & KNN_DEV_TIMEOUT)
@@ -208,13 +261,19 @@ static knn_status bound_common(knn_db *db, const float *query, int64_t m, float 
 extern "C" knn_status knn_lb_box(knn_db *db, const float *query, int64_t m, float band,
                                  int32_t form, float *out_lb, void *stream)
 {
-    return bound_common(db, query, m, band, form, out_lb, stream, false);
+    return bound_common(db, query, m, band, form, out_lb, stream, 0);
+}
+
+extern "C" knn_status knn_lb_seg(knn_db *db, const float *query, int64_t m, float band,
+                                 int32_t form, float *out_lb, void *stream)
+{
+    return bound_common(db, query, m, band, form, out_lb, stream, 2);
 }
 
 extern "C" knn_status knn_greedy_ub(knn_db *db, const float *query, int64_t m, float band,
                                     int32_t form, float *out_ub, void *stream)
 {
-    return bound_common(db, query, m, band, form, out_ub, stream, true);
+    return bound_common(db, query, m, band, form, out_ub, stream, 1);
 }
 
 // ---------------------------------------------------------------------------

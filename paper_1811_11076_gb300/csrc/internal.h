@@ -78,6 +78,79 @@ size_t lb_queue_floats(int n_sm, int nq);
 void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();
 
+// -- coarse first stage of the LB_Box cascade (segment boxes) ---------------
+// Segment width for a database of point width deff (a power of 4, so that
+// the sqrt(W) scaling of means and boxes is exact).
+inline int coarse_width(int deff) { return deff >= 8 ? 16 : 4; }
+struct SegBoxArgs {
+    const float *env_lo, *env_hi;  // [nq][env_stride] envelopes of one bucket
+    int64_t env_stride;
+    int nq, d;                     // d: point width (deff)
+    int W, nseg;                   // segment width, segments of the bucket's longest series
+    float scale;                   // sqrt(W)
+    float *box_lo, *box_hi;        // out: [nq][box_stride], box_floats used per query
+    int64_t box_stride;
+    int box_floats;                // nseg * d rounded up to whole chunks
+};
+struct CoarseArgs {
+    const float *sg;               // scaled segment means of the database
+    const int64_t *sg_off;         // float offset per series (bucket order)
+    const int *db_len;
+    int W;
+    float inv_w;                   // 1 / W (exact: W is a power of 4)
+    int c_begin, c_end;            // series of this bucket
+    int n_lo, n_hi;
+    const int *q_len;
+    const int *q_order;            // batch queries in tile order (nullable)
+    int nq;
+    float band;
+    const float *box_lo, *box_hi;  // scaled segment boxes, [nq][box_stride]
+    int64_t box_stride;
+    int box_floats;
+    int nseg_hi;                   // segments of the bucket's longest series
+    float M;                       // largest coordinate magnitude in the database
+    const float *thr;
+    float mu_prune;
+    const uint32_t *skip;          // [nq][skip_words] series already scored (nullable)
+    int skip_words;
+    int2 *cq;                      // out: (series, query) pairs within their limit
+    int *cq_count;                 //   (nullable: no queue)
+    int64_t cq_cap;
+    float *out_lb;                 // optional: every bound, [nq][out_lb_stride] (component)
+    int64_t out_lb_stride;
+    unsigned long long *stats;
+    int *status;
+    uint32_t fault_wait_spins;     // tests only: see LbArgs
+};
+struct PairLbArgs {
+    const int2 *cq;                // (series, query) pairs
+    const int *cq_count;
+    int64_t cq_cap;
+    const float *db;
+    const int64_t *db_off;
+    const int *db_len;
+    const float *env_lo, *env_hi;  // [nq][env_stride]
+    int64_t env_stride;
+    const float *thr;
+    float mu_prune;
+    int2 *items;                   // out: DP queue of the bucket's segment
+    float *item_lb;
+    int *n_items;
+    int64_t capacity;
+    unsigned long long *stats;
+    int *status;
+};
+void launch_seg_means(const float *data, const int64_t *off, const int *len, int N, int deff,
+                      int W, const int64_t *sg_off, const int64_t *sg_end, float *sg,
+                      cudaStream_t st);
+void launch_absmax(const float *x, int64_t n, unsigned int *out, cudaStream_t st);
+void launch_seg_boxes(const SegBoxArgs &a, cudaStream_t st);
+// Queries per coarse CTA whose boxes fit in shared memory (0: none).
+int coarse_qtile(int box_floats);
+bool launch_lb_coarse(const CoarseArgs &a, int deff, int form, int n_sm, cudaStream_t st);
+bool launch_lb_pairs(const PairLbArgs &a, int deff, int form, int n_sm, cudaStream_t st);
+void lbc_init_attributes();
+
 // -- greedy upper bound (Algorithm 1) ---------------------------------------
 struct GreedyArgs {
     const float *db;
@@ -258,6 +331,8 @@ enum Stat : int {
     STAT_SEED_CELLS,
     STAT_LB_POINTS,      // (query, series point) pairs bounded by LB_Box
     STAT_LB_KERNELS,     // bit mask of the LB_Box kernels that ran (knn_stats.lb_kernels)
+    STAT_LB_COARSE_PRUNED,  // pairs pruned by the coarse (segment box) stage
+    STAT_LB_SEGMENTS,    // (query, series segment) pairs bounded by the coarse stage
     STAT_COUNT
 };
 

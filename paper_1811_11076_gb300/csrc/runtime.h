@@ -56,6 +56,8 @@ struct Workspace {
     DevBuf out_ids, out_dist, out_counts;
     DevBuf skip;
     DevBuf seed_items, seed_lb, scores, sel, lb_all, qemb, qnorm;
+    DevBuf sbox_lo, sbox_hi;            // coarse stage: segment boxes of the queries
+    DevBuf cq, cq_count;                // coarse stage: pairs passing it, per bucket
     uint64_t generation = 0;            // bumped whenever a buffer moves
 };
 
@@ -120,6 +122,10 @@ struct knn_db {
     int lb_qtile[2] = {0, 0};             // queries per LB pass per distance (0: 16)
     int lb_window[2] = {0, 0};            // LB envelope window in chunks (0: automatic)
     int lb_compact[2] = {0, 0};           // LB compaction: 0 automatic, 1 never, 2 always
+    int lb_coarse[2] = {0, 0};            // coarse first LB stage: 0 automatic, 1 never
+    knn::DevBuf sg, sg_off;               // scaled segment means per series (bucket order)
+    int seg_w = 0;                        // segment width of sg (0: not built)
+    float absmax = 0.f;                   // largest coordinate magnitude of the series
     std::vector<double> seg_ms;           // profile: DP time per segment of the last scan
     std::vector<int> seg_first_bucket;    // first bucket of each segment of the last scan
     ~knn_db()

@@ -31,6 +31,8 @@ struct Plan {
     int64_t qfloats = 0;
     int max_m = 0;
     int64_t env_stride = 0;
+    int64_t box_stride = 0;     // coarse stage: floats of one query's segment boxes
+    std::vector<char> coarse;   // per bucket: the coarse first stage runs
     std::vector<Segment> segs;
     std::vector<int> seg_of_bucket;
     int64_t items_cap = 0;
@@ -114,6 +116,22 @@ knn_status make_plan(knn_db *db, const std::vector<int64_t> &hq_off, int q0, int
         pl.env_stride = std::max<int64_t>(pl.env_stride, (int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
     if (pl.env_stride * 2 * 4 > 200 * 1024)
         return set_error(KNN_ERR_UNSUPPORTED, "envelope larger than shared memory (length x d)");
+    // coarse first stage of the LB_Box cascade: filter mode, buckets whose
+    // shortest series has at least 4 whole segments and whose boxes fit
+    const bool filter = !(p.k > 0 && p.seed_mode == KNN_SEED_LB);
+    pl.coarse.assign(db->buckets.size(), 0);
+    pl.box_stride = 0;
+    if (filter && db->lb_coarse[p.distance] == 0 && db->seg_w > 0) {
+        const int W = db->seg_w;
+        for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
+            const Bucket &b = db->buckets[bi];
+            const int box_floats = std::max(4, (b.n_hi / W + PPC - 1) / PPC * CH);
+            if (b.n_lo >= 4 * W && coarse_qtile(box_floats) > 0) {
+                pl.coarse[bi] = 1;
+                pl.box_stride = std::max<int64_t>(pl.box_stride, box_floats);
+            }
+        }
+    }
 
     // DP segments: at most DP_GROUPS groups of consecutive buckets with
     // similar series counts, so that every DP launch has enough pairs to
@@ -203,6 +221,12 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
     G_(slots, sizeof(unsigned long long) * nq * std::max(pl.kslots, 1));
     G_(ub_slots, sizeof(unsigned long long) * nq * std::max(pl.k, 1));
     G_(items, sizeof(int2) * pl.items_cap);
+    if (pl.box_stride > 0) {
+        G_(sbox_lo, sizeof(float) * nq * pl.box_stride);
+        G_(sbox_hi, sizeof(float) * nq * pl.box_stride);
+        G_(cq, sizeof(int2) * pl.items_cap);
+        G_(cq_count, sizeof(int) * db->buckets.size());
+    }
     G_(item_lb, sizeof(float) * pl.items_cap);
     G_(eps_list, sizeof(unsigned long long) * nq * std::max<int64_t>(pl.eps_cap, 1));
     if (pl.eps_cap > FIN_SMALL_CAP)
@@ -407,6 +431,8 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
 
     // envelope + LB_Box stream per bucket (LB-ordered seeding: store every bound)
     const bool store = pl.seeded && !pl.learned;
+    if (pl.box_stride > 0)
+        cudaMemsetAsync(ws.cq_count.p, 0, sizeof(int) * db->buckets.size(), st);
     for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
         const Bucket &b = db->buckets[bi];
         const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];
@@ -424,6 +450,83 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
         e.lo = ws.env_lo.as<float>();
         e.hi = ws.env_hi.as<float>();
         launch_envelope(e, st);
+        if (pl.coarse[bi]) {
+            // coarse bound over segment boxes, then the exact LB_Box of the
+            // pairs it cannot prune; survivors go to the DP queue
+            const int W = db->seg_w;
+            const int nseg = b.n_hi / W;
+            const int box_floats = std::max(4, (nseg + PPC - 1) / PPC * CH);
+            SegBoxArgs sb{};
+            sb.env_lo = ws.env_lo.as<float>();
+            sb.env_hi = ws.env_hi.as<float>();
+            sb.env_stride = pl.env_stride;
+            sb.nq = nq;
+            sb.d = db->deff;
+            sb.W = W;
+            sb.nseg = nseg;
+            sb.scale = W == 16 ? 4.f : 2.f;
+            sb.box_lo = ws.sbox_lo.as<float>();
+            sb.box_hi = ws.sbox_hi.as<float>();
+            sb.box_stride = pl.box_stride;
+            sb.box_floats = box_floats;
+            launch_seg_boxes(sb, st);
+            int2 *cq = ws.cq.as<int2>() + (int64_t)nq * b.c_begin;
+            int *cq_count = ws.cq_count.as<int>() + bi;
+            CoarseArgs c{};
+            c.sg = db->sg.as<float>();
+            c.sg_off = db->sg_off.as<int64_t>();
+            c.db_len = db->len.as<int>();
+            c.W = W;
+            c.inv_w = 1.f / (float)W;
+            c.c_begin = b.c_begin;
+            c.c_end = b.c_end;
+            c.n_lo = b.n_lo;
+            c.n_hi = b.n_hi;
+            c.q_len = ws.q_len.as<int>();
+            c.q_order = ws.q_order.as<int>();
+            c.nq = nq;
+            c.band = p.band;
+            c.box_lo = ws.sbox_lo.as<float>();
+            c.box_hi = ws.sbox_hi.as<float>();
+            c.box_stride = pl.box_stride;
+            c.box_floats = box_floats;
+            c.nseg_hi = nseg;
+            c.M = db->absmax;
+            c.thr = ws.thr.as<float>();
+            c.mu_prune = pl.mg.mu_prune;
+            if (pl.learned) {
+                c.skip = ws.skip.as<uint32_t>();
+                c.skip_words = (db->N + 31) / 32;
+            }
+            c.cq = cq;
+            c.cq_count = cq_count;
+            c.cq_cap = (int64_t)nq * (b.c_end - b.c_begin);
+            c.stats = stats;
+            c.status = &ctrl->status;
+            c.fault_wait_spins = fault_wait_spins();
+            launch_lb_coarse(c, db->deff, kind, db->n_sm, st);
+            PairLbArgs pr{};
+            pr.cq = cq;
+            pr.cq_count = cq_count;
+            pr.cq_cap = c.cq_cap;
+            pr.db = db->data.as<float>();
+            pr.db_off = db->off.as<int64_t>();
+            pr.db_len = db->len.as<int>();
+            pr.env_lo = ws.env_lo.as<float>();
+            pr.env_hi = ws.env_hi.as<float>();
+            pr.env_stride = pl.env_stride;
+            pr.thr = ws.thr.as<float>();
+            pr.mu_prune = pl.mg.mu_prune;
+            pr.items = ws.items.as<int2>() + sg.base;
+            pr.item_lb = ws.item_lb.as<float>() + sg.base;
+            pr.n_items = &ctrl->seg_count[pl.seg_of_bucket[bi]];
+            pr.capacity = sg.cap;
+            pr.stats = stats;
+            pr.status = &ctrl->status;
+            launch_lb_pairs(pr, db->deff, kind, db->n_sm, st);
+            launches += 4;
+            continue;
+        }
         LbArgs l{};
         l.db = db->data.as<float>();
         l.db_off = db->off.as<int64_t>();
@@ -843,6 +946,8 @@ extern "C" knn_status knn_scan(knn_db *db, const float *queries, const int64_t *
         stats->ms_dp = stage_ms[2];
         stats->ms_finalize = stage_ms[3];
         stats->lb_kernels = (int64_t)hc.stats[STAT_LB_KERNELS];
+        stats->lb_coarse_pruned = (int64_t)hc.stats[STAT_LB_COARSE_PRUNED];
+        stats->lb_segments = (int64_t)hc.stats[STAT_LB_SEGMENTS];
     }
     if (hc.status & KNN_DEV_TIMEOUT)
         return set_error(KNN_ERR_TIMEOUT, "a device wait gave up");

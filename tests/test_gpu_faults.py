@@ -3,7 +3,8 @@
 Host side: KNN_FAULT_INJECT=alloc_after:N makes the library's N+1-th device
 allocation fail; every entry point must return KNN_ERR_OOM, release what it
 had allocated, and leave the database usable.  Device side:
-KNN_FAULT_INJECT=wait makes the LB_Box launch run one bounded wait on a
+KNN_FAULT_INJECT=wait makes the LB_Box launches (the coarse first stage or
+the LB_Box stream, whichever runs) run one bounded wait on a
 barrier that nothing completes (nothing is in flight on it); the wait gives
 up after a short limit, the kernel reports it in the status word, and the
 scan returns KNN_ERR_TIMEOUT.  The context stays usable in both cases.

@@ -513,3 +513,73 @@ def test_autotune_and_cache(kw, tmp_path):
     e = entries[0]
     assert db2.get_dp_shape(0, e["r"], e["n"]) == (e["P"], e["G"])
     db2.close()
+
+
+# ---------------------------------------------------------------------------
+# coarse first stage of the LB_Box cascade (segment boxes)
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8, 12, 16])
+@pytest.mark.parametrize("form", [0, 1])
+def test_lb_seg_component(kw, d, form):
+    """knn_lb_seg against the oracle's segment-box bound (same W, same band
+    radius), and never above knn_lb_box."""
+    rng = np.random.default_rng(70 + d + 10 * form)
+    L = 96 if d >= 8 else 50
+    w = make_workload(n_series=300, n_queries=2, d=d, length=L, n_classes=4, seed=60 + d)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    _, W = db.get_lb_cascade(0)
+    assert W == (16 if d >= 8 else 4)
+    band = 0.1
+    r = oracle.band_radius(L, L, f32(band))
+    for qi in range(2):
+        q = w.query(qi)
+        got = db.lb_seg(cuda(q), band, form).cpu().numpy().astype(np.float64)
+        box = db.lb_box(cuda(q), band, form).cpu().numpy().astype(np.float64)
+        exp = np.array([oracle.lb_seg(w.series(c), q, r, W, form) for c in range(300)])
+        scale = max(1.0, float(exp.max()))
+        np.testing.assert_allclose(got, exp, rtol=1e-5, atol=1e-6 * scale)
+        assert np.all(got <= box * (1 + 1e-5) + 1e-6 * scale)
+    db.close()
+
+
+@pytest.mark.parametrize("d,lengths", [(3, None), (3, (40, 200)), (8, (64, 160)), (16, None)])
+def test_coarse_stage_gives_identical_results(kw, d, lengths):
+    """Scans with the coarse first stage (default) and without it return the
+    same rows bit for bit, for DTW and DK, k-NN under every seeding and
+    eps-NN; the stage runs and prunes."""
+    L = 128 if d == 16 else 80
+    w = make_workload(n_series=2500, n_queries=12, d=d, length=L, length_range=lengths,
+                      n_classes=8, seed=90 + d)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    q = cuda(w.q)
+    enc = kw.Encoder(d, seed=3)
+    enc.attach(db)
+    for kind in (kw.DTW, kw.DK):
+        for seed in (kw.SEED_LEARNED, kw.SEED_GREEDY, kw.SEED_NONE):
+            db.set_lb_cascade(kind, 0)
+            on = db.scan(q, w.q_off, k=6, band=0.1, distance=kind, seed=seed, stats=True)
+            db.set_lb_cascade(kind, 1)
+            off = db.scan(q, w.q_off, k=6, band=0.1, distance=kind, seed=seed, stats=True)
+            np.testing.assert_array_equal(on[0].cpu().numpy(), off[0].cpu().numpy())
+            np.testing.assert_array_equal(on[1].cpu().numpy(), off[1].cpu().numpy())
+            assert on[2]["lb_kernels"] & 16 and not off[2]["lb_kernels"] & 16
+            assert off[2]["lb_coarse_pruned"] == 0
+            assert on[2]["lb_pruned"] == off[2]["lb_pruned"]
+            if seed != kw.SEED_NONE:  # without seeding the threshold is +inf at LB time
+                assert on[2]["lb_coarse_pruned"] > 0
+                assert on[2]["lb_points"] < off[2]["lb_points"]
+        if lengths is None:
+            oi, od = oracle.knn(w.db, w.db_off, w.q, w.q_off, band=f32(0.1), kind=kind, k=6)
+            db.set_lb_cascade(kind, 0)
+            ids, dist = db.scan(q, w.q_off, k=6, band=0.1, distance=kind, seed=kw.SEED_LEARNED)
+            check_knn(ids.cpu().numpy(), dist.cpu().numpy(), oi, od, kind, 6)
+        eps = float(np.float32(np.median(on[1].cpu().numpy()[:, 3])))
+        res = []
+        for coarse in (0, 1):
+            db.set_lb_cascade(kind, coarse)
+            res.append(db.scan(q, w.q_off, k=0, eps=eps, eps_capacity=2500, band=0.1,
+                               distance=kind))
+        for a, b in zip(res[0], res[1]):
+            np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    enc.close()
+    db.close()

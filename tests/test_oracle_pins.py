@@ -240,6 +240,33 @@ def test_lb_box_brute_small(orc):
     assert lbm <= worst + 1e-12 and worst - lbm < 1e-4 * (1.0 + worst)
 
 
+def test_segment_box_bound(orc):
+    """The cascade's coarse stage: with W = 1 it is LB_Box itself (each
+    segment one point, its box B_i); for every W it never exceeds LB_Box (in
+    either form); hand-worked values."""
+    import json
+    import os
+    rng = np.random.default_rng(21)
+    for _ in range(60):
+        d = int(rng.integers(1, 5))
+        m = int(rng.integers(4, 40))
+        n = int(np.clip(m + rng.integers(-3, 4), 2, None))
+        r = int(rng.integers(abs(m - n), 10))
+        s, t = rand_series(rng, m, d), rand_series(rng, n, d)
+        for form in (0, 1):
+            box = orc.lb_box(s, t, r, form=form)
+            assert orc.lb_seg(s, t, r, 1, form) == pytest.approx(box, rel=1e-12, abs=1e-12)
+            for W in (2, 4, 16):
+                assert orc.lb_seg(s, t, r, W, form) <= box * (1 + 1e-12) + 1e-12
+    with open(os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")) as f:
+        cases = json.load(f)["segment_box_cases"]
+    for c in cases:
+        s, t = np.array(c["S"], dtype=float), np.array(c["T"], dtype=float)
+        assert orc.lb_seg(s, t, c["r"], c["W"], 0) == pytest.approx(c["lb_seg"], rel=1e-12), c["name"]
+        assert orc.lb_seg(s, t, c["r"], c["W"], 1) == pytest.approx(c["lb_seg_max"], rel=1e-12)
+        assert orc.lb_box(s, t, c["r"]) == pytest.approx(c["lb_box"], rel=1e-12), c["name"]
+
+
 # ---------------------------------------------------------------------------
 # Section 4: GDK, sparse DK, early abandoning
 
