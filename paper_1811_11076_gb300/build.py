@@ -31,6 +31,72 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+# Point widths with DP kernels compiled (one translation unit each, so that
+# nvcc compiles them in parallel); the units are generated from DP_UNIT.
+DP_WIDTHS = (1, 2, 3, 4, 5, 6, 7, 8, 16)
+GEN = os.path.join(BUILD, "gen")
+DP_UNIT = """// Generated by build.py: DP kernel instantiations for d = {D}.
+#include "dp.cuh"
+#include "dp_variants.h"
+
+namespace knn {{
+
+namespace {{
+template <int DD, int PP>
+bool try_launch(const DpArgs &a, int P, int kind, int n_sm, cudaStream_t st)
+{{
+    if constexpr (DD == {D}) {{
+        if (P == PP)
+            return dp_launch_tpl<DD, PP>(a, kind, n_sm, st);
+    }}
+    return false;
+}}
+template <int DD, int PP>
+int try_occ(int P, int kind)
+{{
+    if constexpr (DD == {D}) {{
+        if (P == PP)
+            return dp_occupancy_tpl<DD, PP>(kind);
+    }}
+    return 0;
+}}
+}}  // namespace
+
+bool dp_launch_d{D}(const DpArgs &a, int P, int kind, int n_sm, cudaStream_t st)
+{{
+#define KNN_X(DD, PP) if (try_launch<DD, PP>(a, P, kind, n_sm, st)) return true;
+    KNN_DP_VARIANTS(KNN_X)
+#undef KNN_X
+    return false;
+}}
+
+int dp_occ_d{D}(int P, int kind)
+{{
+    int v = 0;
+#define KNN_X(DD, PP) v += try_occ<DD, PP>(P, kind);
+    KNN_DP_VARIANTS(KNN_X)
+#undef KNN_X
+    return v;
+}}
+
+}}  // namespace knn
+"""
+
+
+def generated_units() -> list[str]:
+    """Write the per-width DP units (only when their text changes)."""
+    os.makedirs(GEN, exist_ok=True)
+    out = []
+    for d in DP_WIDTHS:
+        path = os.path.join(GEN, f"dp_d{d}.cu")
+        text = DP_UNIT.format(D=d)
+        if not os.path.exists(path) or open(path).read() != text:
+            with open(path, "w") as f:
+                f.write(text)
+        out.append(path)
+    return out
+
+
 def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -41,6 +107,7 @@ def _digest(paths) -> str:
         with open(p, "rb") as f:
             h.update(p.encode() + b"\0" + f.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(DP_UNIT.encode() + repr(DP_WIDTHS).encode())
     return h.hexdigest()
 
 
@@ -61,12 +128,12 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
             if f.read().strip() == digest:
                 return LIB
     cc = nvcc()
-    srcs = sources()
+    srcs = sources() + generated_units()
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, "-I" + CSRC, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

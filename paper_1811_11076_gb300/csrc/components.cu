@@ -405,8 +405,7 @@ extern "C" knn_status knn_pairwise(const float *a, const int64_t *a_off, const f
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const int occ = dp_max_blocks_per_sm(deff, P, distance);
-        if (!launch_dp(x, deff, P, distance, nsm * std::max(occ, 1), st)) {
+        if (!launch_dp(x, deff, P, distance, nsm, st)) {
             cudaStreamSynchronize(st);
             return set_error(KNN_ERR_UNSUPPORTED, "no DP kernel compiled for this d and shape");
         }

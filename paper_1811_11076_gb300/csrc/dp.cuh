@@ -397,37 +397,53 @@ constexpr bool dp_has_win()
     return D >= 8 && D <= 16 && D % 4 == 0 && (P & (P - 1)) == 0 && P >= 2 && P <= 16;
 }
 
+// Resident CTAs per SM of one kernel with the given dynamic shared memory,
+// looked up once per kernel (the persistent grid is SMs x this).
+template <typename K>
+int dp_blocks_for(K kernel, size_t smem)
+{
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, DP_THREADS, smem);
+    return blocks > 0 ? blocks : 1;
+}
+
+template <int D, int P, int KIND, bool WIN>
+void dp_launch_one(const DpArgs &a, int n_sm, size_t smem, cudaStream_t st)
+{
+    static int blocks = 0;
+    if (!blocks) {
+        if (smem > 48 * 1024) {
+            cudaFuncSetAttribute(dp_kernel<D, P, KIND, WIN>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(dp_kernel<D, P, KIND, WIN>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        }
+        blocks = dp_blocks_for(dp_kernel<D, P, KIND, WIN>, smem);
+    }
+    dp_kernel<D, P, KIND, WIN><<<n_sm * blocks, DP_THREADS, smem, st>>>(a);
+}
+
+// Launch the variant for the pair shape (the shared-memory window where a
+// point is wide and a group has lanes enough to load it); the persistent
+// grid is SMs x the resident CTAs of that variant.
 template <int D, int P>
-bool dp_launch_tpl(const DpArgs &a, int kind, int grid, cudaStream_t st)
+bool dp_launch_tpl(const DpArgs &a, int kind, int n_sm, cudaStream_t st)
 {
     if constexpr (dp_has_win<D, P>()) {
         if (a.G >= 8) {
             const size_t smem = dp_win_bytes(D, P);
-            static bool attr = false;
-            if (!attr) {
-                cudaFuncSetAttribute(dp_kernel<D, P, 0, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                cudaFuncSetAttribute(dp_kernel<D, P, 1, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                cudaFuncSetAttribute(dp_kernel<D, P, 0, true>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared);
-                cudaFuncSetAttribute(dp_kernel<D, P, 1, true>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared);
-                attr = true;
-            }
             if (kind == 0)
-                dp_kernel<D, P, 0, true><<<grid, DP_THREADS, smem, st>>>(a);
+                dp_launch_one<D, P, 0, true>(a, n_sm, smem, st);
             else
-                dp_kernel<D, P, 1, true><<<grid, DP_THREADS, smem, st>>>(a);
+                dp_launch_one<D, P, 1, true>(a, n_sm, smem, st);
             return true;
         }
     }
     if (kind == 0)
-        dp_kernel<D, P, 0, false><<<grid, DP_THREADS, 0, st>>>(a);
+        dp_launch_one<D, P, 0, false>(a, n_sm, 0, st);
     else
-        dp_kernel<D, P, 1, false><<<grid, DP_THREADS, 0, st>>>(a);
+        dp_launch_one<D, P, 1, false>(a, n_sm, 0, st);
     return true;
 }
 

@@ -1,28 +1,29 @@
-// Dispatch over the compiled (D, P) variants of the DP kernel.
+// Dispatch over the compiled (D, P) variants of the DP kernel (one unit per
+// width, generated by build.py).
 #include "dp.cuh"
 #include "dp_variants.h"
 
 namespace knn {
 
 #define KNN_DECL(D)                                                                  \
-    bool dp_launch_d##D(const DpArgs &a, int P, int kind, int grid, cudaStream_t st); \
+    bool dp_launch_d##D(const DpArgs &a, int P, int kind, int n_sm, cudaStream_t st); \
     int dp_occ_d##D(int P, int kind);
 KNN_DECL(1) KNN_DECL(2) KNN_DECL(3) KNN_DECL(4) KNN_DECL(5) KNN_DECL(6) KNN_DECL(7) KNN_DECL(8)
 KNN_DECL(16)
 #undef KNN_DECL
 
-bool launch_dp(const DpArgs &a, int d, int P, int kind, int grid, cudaStream_t st)
+bool launch_dp(const DpArgs &a, int d, int P, int kind, int n_sm, cudaStream_t st)
 {
     switch (d) {
-    case 1: return dp_launch_d1(a, P, kind, grid, st);
-    case 2: return dp_launch_d2(a, P, kind, grid, st);
-    case 3: return dp_launch_d3(a, P, kind, grid, st);
-    case 4: return dp_launch_d4(a, P, kind, grid, st);
-    case 5: return dp_launch_d5(a, P, kind, grid, st);
-    case 6: return dp_launch_d6(a, P, kind, grid, st);
-    case 7: return dp_launch_d7(a, P, kind, grid, st);
-    case 8: return dp_launch_d8(a, P, kind, grid, st);
-    case 16: return dp_launch_d16(a, P, kind, grid, st);
+    case 1: return dp_launch_d1(a, P, kind, n_sm, st);
+    case 2: return dp_launch_d2(a, P, kind, n_sm, st);
+    case 3: return dp_launch_d3(a, P, kind, n_sm, st);
+    case 4: return dp_launch_d4(a, P, kind, n_sm, st);
+    case 5: return dp_launch_d5(a, P, kind, n_sm, st);
+    case 6: return dp_launch_d6(a, P, kind, n_sm, st);
+    case 7: return dp_launch_d7(a, P, kind, n_sm, st);
+    case 8: return dp_launch_d8(a, P, kind, n_sm, st);
+    case 16: return dp_launch_d16(a, P, kind, n_sm, st);
     default: return false;
     }
 }

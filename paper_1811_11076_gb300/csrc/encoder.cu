@@ -1053,8 +1053,7 @@ extern "C" knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_
     x.cells_stat = STAT_DP_CELLS;
     x.stats = ct->stats;
     x.status = &ct->status;
-    const int occ = dp_max_blocks_per_sm(db->deff, P, tp->distance);
-    launch_dp(x, db->deff, P, tp->distance, db->n_sm * std::max(occ, 1), st);
+    launch_dp(x, db->deff, P, tp->distance, db->n_sm, st);
     pair_targets_kernel<<<256, 256, 0, st>>>(draw.as<float>(), db->len.as<int>(), db->len.as<int>(),
                                              ditems.as<int2>(), np, tp->distance,
                                              dtgt.as<float>());

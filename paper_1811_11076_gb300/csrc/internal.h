@@ -243,8 +243,9 @@ struct DpArgs {
     unsigned long long *stats;
     int *status;
 };
-// Returns false if no kernel is compiled for (d, P).
-bool launch_dp(const DpArgs &a, int d, int P, int kind, int grid, cudaStream_t st);
+// Returns false if no kernel is compiled for (d, P).  The persistent grid is
+// n_sm times the resident CTAs of the variant that runs.
+bool launch_dp(const DpArgs &a, int d, int P, int kind, int n_sm, cudaStream_t st);
 int dp_block_threads();
 // Largest P compiled for this d, and the list of compiled P values.
 int dp_num_variants(int d);

@@ -293,8 +293,7 @@ extern "C" knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off,
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int occ = dp_max_blocks_per_sm(deff, P, distance);
-    if (!launch_dp(x, deff, P, distance, nsm * (occ > 0 ? occ : 1), st)) {
+    if (!launch_dp(x, deff, P, distance, nsm, st)) {
         cudaStreamSynchronize(st);  // retire the two launches already enqueued
         return set_error(KNN_ERR_UNSUPPORTED, "no DP kernel compiled for this d and shape");
     }

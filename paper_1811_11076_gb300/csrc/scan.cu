@@ -422,8 +422,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
                            &ctrl->n_seed, (int64_t)nq * pl.S, &ctrl->seed_head);
         a.G = pl.seed_dp.G;
         a.cells_stat = STAT_SEED_CELLS;
-        const int occ = dp_max_blocks_per_sm(db->deff, pl.seed_dp.P, kind);
-        launch_dp(a, db->deff, pl.seed_dp.P, kind, db->n_sm * std::max(occ, 1), st);
+        launch_dp(a, db->deff, pl.seed_dp.P, kind, db->n_sm, st);
         launches += 9;
     }
     if (sev)
@@ -593,8 +592,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
                            &ctrl->n_seed, (int64_t)nq * pl.S, &ctrl->seed_head);
         a.G = pl.seed_dp.G;
         a.cells_stat = STAT_SEED_CELLS;
-        const int occ = dp_max_blocks_per_sm(db->deff, pl.seed_dp.P, kind);
-        launch_dp(a, db->deff, pl.seed_dp.P, kind, db->n_sm * std::max(occ, 1), st);
+        launch_dp(a, db->deff, pl.seed_dp.P, kind, db->n_sm, st);
         launches += 2;
     }
     if (sev)
@@ -633,8 +631,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
                            &ctrl->seg_count[si], sg.cap, &ctrl->seg_head[si]);
         a.G = sg.G;
         a.cells_stat = STAT_DP_CELLS;
-        const int occ = dp_max_blocks_per_sm(db->deff, sg.P, kind);
-        launch_dp(a, db->deff, sg.P, kind, db->n_sm * std::max(occ, 1), st);
+        launch_dp(a, db->deff, sg.P, kind, db->n_sm, st);
         ++launches;
     }
     if (sev) {
