@@ -59,6 +59,34 @@ __device__ __forceinline__ void load_point_prefix(const float *p, int idx, int l
     load_point<D>(p + clampi(idx, -1, last) * D, v);
 }
 
+// Squared distance of two wide points on packed FP32 pairs: two interleaved
+// partial sums (even and odd coordinates), each an FMA chain, joined at the
+// end and added to `init` (0, or +inf for an out-of-band slot).  Half the
+// instructions of the scalar chain and half its dependent length; the sum has
+// at most D/2 + 2 roundings per term, within the (d + 2) u bound.
+template <int D>
+__device__ __forceinline__ float sqdist_acc_p2(const float (&a)[D], const float (&b)[D], float init)
+{
+    static_assert(D % 2 == 0, "pairs of coordinates");
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < D; k += 2) {
+        const float2 t = sub2(make_float2(a[k], a[k + 1]), make_float2(b[k], b[k + 1]));
+        acc = __ffma2_rn(t, t, acc);
+    }
+    return (acc.x + acc.y) + init;
+}
+
+// Point cost of the DP: packed pairs from d = 8 on.
+template <int D>
+__device__ __forceinline__ float dp_cost(const float (&a)[D], const float (&b)[D], float init)
+{
+    if constexpr (D >= 8 && D % 2 == 0)
+        return sqdist_acc_p2<D>(a, b, init);
+    else
+        return sqdist_acc<D>(a, b, init);
+}
+
 // Rows of the shared-memory window of one lane group (WIN kernels): the
 // newest row any lane reads and the G-1 strides of P below it, plus one, as
 // a power of two.
@@ -290,7 +318,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
             up = (lam == 0) ? KNN_INF : up;
 #pragma unroll
             for (int e = 0; e < P; ++e) {
-                const float c = sqdist_acc<D>(qw[((u - e) % U + U) % U], xw[(u + e) % U], mE[e]);
+                const float c = dp_cost<D>(qw[((u - e) % U + U) % U], xw[(u + e) % U], mE[e]);
                 const float left = (e == 0) ? up : O[e - 1];
                 const float mn = fmin3(left, O[e], E[e]);
                 E[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
@@ -300,7 +328,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
 #pragma unroll
             for (int e = 0; e < P; ++e) {
                 const float c =
-                    sqdist_acc<D>(qw[((u - e) % U + U) % U], xw[(u + e + 1) % U], mO[e]);
+                    dp_cost<D>(qw[((u - e) % U + U) % U], xw[(u + e + 1) % U], mO[e]);
                 const float right = (e == P - 1) ? dn : E[e + 1];
                 const float mn = fmin3(E[e], right, O[e]);
                 O[e] = (KIND == 0) ? c + mn : fmaxf(c, mn);
