@@ -151,6 +151,19 @@ typedef struct knn_encoder knn_encoder;
 KNN_API knn_status knn_db_create(const float *series, const int64_t *offsets,
                                  int64_t n_series, int32_t d, void *stream,
                                  knn_db **out);
+/* A database whose series are the windows T[a .. a+m-1] of one long series
+ * T (n points, [n][d] point-major, host or device), a = 0, stride,
+ * 2 stride, ... up to n - m: series id i starts at point i * stride.  A
+ * knn_scan of queries of length m against it is the banded subsequence
+ * search (every window of T against the query under the Sakoe-Chiba band of
+ * Section 2.2, the whole-match DTW / DK of Section 2.1), with every feature
+ * of the scan: k best windows or all within eps, exact order, the LB_Box
+ * cascade and early abandoning.  Windows overlap; no exclusion zone is
+ * applied (the next best windows are usually neighbours of the best).  The
+ * layout stores each window separately: (n - m) / stride + 1 windows of m
+ * points.  1 <= m <= 65536, stride >= 1. */
+KNN_API knn_status knn_db_create_windows(const float *series, int64_t n, int32_t d, int32_t m,
+                                         int32_t stride, void *stream, knn_db **out);
 KNN_API knn_status knn_db_destroy(knn_db *db);
 /* Number of series and dimensionality. */
 KNN_API knn_status knn_db_info(const knn_db *db, int64_t *n_series, int32_t *d,
@@ -343,14 +356,33 @@ KNN_API knn_status knn_pairwise_noalloc(const float *a, const int64_t *a_off, in
  * subsequence (the smallest b on ties).  eps >= 0 (+inf: none): cells whose
  * value exceeds eps (DTW units for DTW, Euclidean for DK) are dropped (values
  * only grow along a path; for DK this is Algorithm 3's sparse visit); a
- * result above eps is reported as +inf with end -1.  queries/q_offsets as in knn_scan; series, queries and
- * outputs may be host or device memory.  Limits: 1 <= d <= 16; m <= 1024
- * for d = 1, 512 for d = 2, 3, 256 for d = 4..8, 128 for d = 9..16 (else
- * KNN_ERR_UNSUPPORTED); coordinates of magnitude well below 1e18 (sentinel
- * points of that value pad T).  Synchronises `stream`. */
+ * result above eps is reported as +inf with end -1.  queries/q_offsets as
+ * in knn_scan; series, queries and outputs may be host or device memory.
+ * Exactness: the FP32 sweep keeps the 9 best ends of each query; the best
+ * and those within 2e-4 (relative) of it, far beyond the FP32 rounding of
+ * a path, are re-scored in FP64 over the columns a path of their value can
+ * span (the walk back from b stops where the least cell cost per column,
+ * summed for DTW, single for DK, exceeds the FP32 value by 0.1 %), and the
+ * best by (FP64 value, end) is reported.  Limits: 1 <= d <= 16; m <= 1024 for d = 1, 512
+ * for d = 2, 3, 256 for d = 4..8, 128 for d = 9..16 (else
+ * KNN_ERR_UNSUPPORTED); a re-scored match spanning more than 65,536 columns
+ * returns KNN_ERR_UNSUPPORTED; coordinates of magnitude well below 1e18
+ * (sentinel points of that value pad T).  Synchronises `stream`. */
 KNN_API knn_status knn_subseq(const float *queries, const int64_t *q_offsets, int32_t n_queries,
                               const float *series, int64_t n, int32_t d, int32_t distance,
                               float eps, float *out_dist, int64_t *out_end, void *stream);
+
+/* The k best end columns of the same search (1 <= k <= 16): out_dist and
+ * out_end are [n_queries][k], ordered by (value, end), padded with +inf / -1
+ * where fewer than k ends lie within eps.  The FP32 sweep keeps the
+ * k + max(8, k) best ends; the k best and those within 2e-4 of the k-th are
+ * re-scored in FP64 as for knn_subseq.  Ends
+ * next to the best usually come next (a subsequence and its neighbours match
+ * nearly as well); no exclusion zone is applied. */
+KNN_API knn_status knn_subseq_k(const float *queries, const int64_t *q_offsets,
+                                int32_t n_queries, const float *series, int64_t n, int32_t d,
+                                int32_t distance, int32_t k, float eps, float *out_dist,
+                                int64_t *out_end, void *stream);
 
 /* Algorithm 2 (greedy dog-keeper for subsequence search): per query the
  * largest Euclidean cost along the greedy walk that starts at row 0 in the

@@ -69,6 +69,9 @@ def lib():
                                      C.c_double, C.c_int]
             L.orc_sub_distance.restype = C.c_double
             L.orc_sub_distance.argtypes = [C.c_int, _d, C.c_int64, _d, C.c_int64, C.c_int, _i64]
+            L.orc_sub_ends.restype = C.c_int64
+            L.orc_sub_ends.argtypes = [C.c_int, _d, C.c_int64, _d, C.c_int64, C.c_int, C.c_int64,
+                                       _d, _i64]
             L.orc_sub_sparse_dk.restype = C.c_double
             L.orc_sub_sparse_dk.argtypes = [_d, C.c_int64, _d, C.c_int64, C.c_int, C.c_double,
                                             _i64, _i64]
@@ -195,6 +198,17 @@ def sub_distance(kind: int, s, t):
     end = C.c_int64(-1)
     v = lib().orc_sub_distance(kind, _p(s), m, _p(t), n, d, C.byref(end))
     return v, end.value
+
+
+def sub_ends(kind: int, s, t, k: int):
+    """The k best end columns of subsequence search (the free-start recursion
+    of sub_distance): the k smallest (D(m, b), b) over every column b, ordered
+    by (value, b).  Returns (values[k], ends[k]), padded with +inf / -1."""
+    s, t, m, n, d = _pair_args(s, t)
+    val = np.empty(k)
+    end = np.empty(k, dtype=np.int64)
+    lib().orc_sub_ends(kind, _p(s), m, _p(t), n, d, k, _p(val), _p(end, _i64))
+    return val, end
 
 
 def sub_sparse_dk(s, t, eps: float):

@@ -461,6 +461,56 @@ double orc_sub_distance(int kind, const double *s, int64_t m, const double *t, i
     return best;
 }
 
+/* The k best end columns of subsequence search (the free-start recursion of
+ * orc_sub_distance): every column b of T ends a best match of value D(m, b),
+ * the minimum over all starts a <= b; the k smallest (value, b) pairs, in
+ * that order (equal values: the smaller b first), are written to val / end
+ * (padded with +inf / -1).  Returns how many were written. */
+int64_t orc_sub_ends(int kind, const double *s, int64_t m, const double *t, int64_t n, int d,
+                     int64_t k, double *val, int64_t *end)
+{
+    for (int64_t j = 0; j < k; ++j) {
+        val[j] = ORC_INF;
+        end[j] = -1;
+    }
+    if (m <= 0 || n <= 0 || k <= 0)
+        return 0;
+    double *prev = malloc(sizeof(double) * (size_t)m);
+    double *cur = malloc(sizeof(double) * (size_t)m);
+    for (int64_t i = 0; i < m; ++i)
+        prev[i] = ORC_INF;
+    int64_t cnt = 0;
+    for (int64_t b = 0; b < n; ++b) {
+        for (int64_t i = 0; i < m; ++i) {
+            const double c = kind == ORC_DTW ? sqdist(s + i * d, t + b * d, d)
+                                             : eucl(s + i * d, t + b * d, d);
+            const double pred = i == 0 ? 0.0 : fmin(fmin(cur[i - 1], prev[i]), prev[i - 1]);
+            cur[i] = kind == ORC_DTW ? c + pred : fmax(c, pred);
+        }
+        /* insert (cur[m-1], b) into the sorted list; b grows, so it goes after
+         * every equal value */
+        const double v = cur[m - 1];
+        if (cnt < k || v < val[k - 1]) {
+            int64_t p = cnt < k ? cnt : k - 1;
+            while (p > 0 && val[p - 1] > v) {
+                val[p] = val[p - 1];
+                end[p] = end[p - 1];
+                --p;
+            }
+            val[p] = v;
+            end[p] = b;
+            if (cnt < k)
+                ++cnt;
+        }
+        double *tmp = prev;
+        prev = cur;
+        cur = tmp;
+    }
+    free(prev);
+    free(cur);
+    return cnt;
+}
+
 /* Sparse dog-keeper distance for subsequence search (Algorithm 3 with
  * SUB = true): the column sweep of orc_sparse_dk without a band, where row 1
  * joins the rows to visit in every column (a match may start anywhere) and

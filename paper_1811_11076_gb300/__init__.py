@@ -39,7 +39,7 @@ EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_sc
            "knn_envelope", "knn_lb_box", "knn_greedy_ub", "knn_pairwise", "knn_status_string",
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
            "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_set_lb_cascade",
-           "knn_get_lb_cascade", "knn_lb_seg", "knn_subseq", "knn_subseq_greedy", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
+           "knn_get_lb_cascade", "knn_lb_seg", "knn_subseq", "knn_subseq_k", "knn_db_create_windows", "knn_subseq_greedy", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
            "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach",
            "knn_encoder_params", "knn_encoder_loss_grad", "knn_encoder_save", "knn_encoder_load")
 
@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
     vp, i64p = C.c_void_p, C.c_void_p
     L.knn_db_create.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.POINTER(vp)]
     L.knn_db_destroy.argtypes = [vp]
+    L.knn_db_create_windows.argtypes = [vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32, vp,
+                                        C.POINTER(vp)]
     L.knn_db_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                               C.POINTER(C.c_int32)]
     L.knn_scan.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(Params), vp, vp, vp,
@@ -119,6 +121,8 @@ def lib() -> C.CDLL:
     L.knn_dp_shapes.argtypes = [C.c_int32, vp, C.c_int32]
     L.knn_subseq.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, C.c_int32, C.c_int32, C.c_float,
                              vp, vp, vp]
+    L.knn_subseq_k.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                               C.c_float, vp, vp, vp]
     L.knn_subseq_greedy.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, C.c_int32, C.c_float, vp,
                                     vp, vp]
     L.knn_set_lb_tile.argtypes = [vp] + [C.c_int32] * 4
@@ -205,6 +209,25 @@ class KnnDB:
         self._keep = None
         self.d = int(d)
         self.n = int(offsets.shape[0] - 1)
+
+    @classmethod
+    def windows(cls, series, m: int, stride: int = 1, stream=None) -> "KnnDB":
+        """The windows T[a .. a+m-1] of one long series T [n][d] (a = 0,
+        stride, ...): a scan of length-m queries against it is the banded
+        subsequence search; result ids are window indices (start = id *
+        stride)."""
+        series = _f32(series)
+        d = int(series.shape[1]) if len(series.shape) == 2 else 1
+        n = int(series.shape[0])
+        h = C.c_void_p()
+        _check(lib().knn_db_create_windows(_ptr(series), n, d, int(m), int(stride),
+                                           _stream(stream), C.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        self._keep = None
+        self.d = d
+        self.n = (n - int(m)) // int(stride) + 1
+        return self
 
     @property
     def handle(self):
@@ -413,11 +436,12 @@ class Encoder:
 
 
 def subseq(queries, q_offsets, series, *, distance: int = DK, eps: float = float("inf"),
-           greedy: bool = False, stream=None):
+           greedy: bool = False, k: int = 1, stream=None):
     """Subsequence search of every query against one long series (Section 4.2,
     Algorithm 3 with SUB = true; greedy=True: the Algorithm 2 upper bound).
     queries [sum m][d], q_offsets [nq+1], series [n][d]: host or device.
-    Returns (values [nq] float32, ends [nq] int64) on the inputs' device."""
+    Returns (values, ends) on the inputs' device: [nq] for k = 1, else
+    [nq][k], the k best end columns by (value, end)."""
     import torch
     queries = _f32(queries)
     q_offsets = _i64(q_offsets)
@@ -426,16 +450,21 @@ def subseq(queries, q_offsets, series, *, distance: int = DK, eps: float = float
     d = int(series.shape[1]) if series.ndim > 1 else 1
     on_gpu = hasattr(series, "is_cuda") and series.is_cuda
     dev = series.device if on_gpu else torch.device("cpu")
-    vals = torch.empty(nq, dtype=torch.float32, device=dev)
-    ends = torch.empty(nq, dtype=torch.int64, device=dev)
+    shape = (nq,) if k == 1 or greedy else (nq, k)
+    vals = torch.empty(shape, dtype=torch.float32, device=dev)
+    ends = torch.empty(shape, dtype=torch.int64, device=dev)
     if greedy:
         _check(lib().knn_subseq_greedy(_ptr(queries), _ptr(q_offsets), nq, _ptr(series),
                                        int(series.shape[0]), d, eps, _ptr(vals), _ptr(ends),
                                        _stream(stream)))
-    else:
+    elif k == 1:
         _check(lib().knn_subseq(_ptr(queries), _ptr(q_offsets), nq, _ptr(series),
                                 int(series.shape[0]), d, distance, eps, _ptr(vals), _ptr(ends),
                                 _stream(stream)))
+    else:
+        _check(lib().knn_subseq_k(_ptr(queries), _ptr(q_offsets), nq, _ptr(series),
+                                  int(series.shape[0]), d, distance, k, eps, _ptr(vals),
+                                  _ptr(ends), _stream(stream)))
     return vals, ends
 
 

@@ -237,44 +237,19 @@ knn_status knn::check_finite_dev(const float *dev, int64_t n, int *flag_dev, cud
     return KNN_OK;
 }
 
-extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets, int64_t n_series,
-                                    int32_t d, void *stream, knn_db **out)
+// Builds the library layout of N series whose point offsets into `series`
+// are hoff[0..N) (hoff[N]: the end of the source points); fixed_len > 0: every
+// series has that length (windows may overlap), else series i ends at
+// hoff[i+1].  Lengths are validated by the caller.
+static knn_status db_build(const float *series, const std::vector<int64_t> &hoff, int N, int32_t d,
+                           int max_len, int fixed_len, cudaStream_t st, knn_db **out)
 {
-    if (!out)
-        return set_error(KNN_ERR_INVALID, "out is NULL");
-    *out = nullptr;
-    if (!series || !offsets)
-        return set_error(KNN_ERR_INVALID, "series/offsets is NULL");
-    if (n_series < 1 || n_series > (int64_t)0x7fffffff)
-        return set_error(KNN_ERR_INVALID, "n_series must be in [1, 2^31)");
-    if (d < 1 || d > 16)
-        return set_error(KNN_ERR_INVALID, "d must be in [1, 16]");
-    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n_series = N;
     const int deff = deff_for(d);
     const int CH = chunk_floats(deff), PPC = chunk_points(deff);
-
-    std::vector<int64_t> hoff(n_series + 1);
-    const bool off_dev = is_device_ptr(offsets);
-    if (off_dev) {
-        cudaError_t e = cudaMemcpy(hoff.data(), offsets, sizeof(int64_t) * (n_series + 1),
-                                   cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess)
-            return cuda_error(e, "copy offsets");
-    } else {
-        memcpy(hoff.data(), offsets, sizeof(int64_t) * (n_series + 1));
-    }
-    if (hoff[0] < 0)
-        return set_error(KNN_ERR_INVALID, "offsets[0] < 0");
-    int max_len = 0;
-    for (int64_t i = 0; i < n_series; ++i) {
-        const int64_t L = hoff[i + 1] - hoff[i];
-        if (L < 1)
-            return set_error(KNN_ERR_INVALID, "series " + std::to_string(i) + " has length < 1");
-        if (L > 65536)
-            return set_error(KNN_ERR_UNSUPPORTED, "series longer than 65536 points");
-        max_len = std::max<int>(max_len, (int)L);
-    }
-    const int N = (int)n_series;
+    auto len_of = [&](int i) -> int64_t {
+        return fixed_len > 0 ? fixed_len : hoff[i + 1] - hoff[i];
+    };
 
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
@@ -296,7 +271,7 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
     for (int i = 0; i < N; ++i)
         order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return hoff[a + 1] - hoff[a] < hoff[b + 1] - hoff[b];
+        return len_of(a) < len_of(b);
     });
     db->h_len.resize(N);
     db->h_len_by_id.resize(N);
@@ -304,7 +279,7 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
     int64_t total = 0;
     for (int c = 0; c < N; ++c) {
         const int id = order[c];
-        const int n = (int)(hoff[id + 1] - hoff[id]);
+        const int n = (int)len_of(id);
         db->h_len[c] = n;
         db->h_len_by_id[id] = n;
         total += CH;  // leading chunk: the DP's sentinel point
@@ -379,7 +354,7 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
         return set_error(KNN_ERR_INVALID, "database contains NaN or Inf");
     }
     launch_repack(src, (const int64_t *)off_stage.p, (const int *)db->id.p, N, d, deff,
-                  (const int64_t *)db->off.p, (float *)db->data.p, st, true);
+                  (const int64_t *)db->off.p, (float *)db->data.p, st, true, fixed_len);
 
     // coarse first stage of the LB_Box cascade: scaled segment means of every
     // series (full segments only) and the largest coordinate magnitude
@@ -424,6 +399,71 @@ extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets,
     db->seg_w = W;
     *out = db;
     return KNN_OK;
+}
+
+extern "C" knn_status knn_db_create(const float *series, const int64_t *offsets, int64_t n_series,
+                                    int32_t d, void *stream, knn_db **out)
+{
+    if (!out)
+        return set_error(KNN_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!series || !offsets)
+        return set_error(KNN_ERR_INVALID, "series/offsets is NULL");
+    if (n_series < 1 || n_series > (int64_t)0x7fffffff)
+        return set_error(KNN_ERR_INVALID, "n_series must be in [1, 2^31)");
+    if (d < 1 || d > 16)
+        return set_error(KNN_ERR_INVALID, "d must be in [1, 16]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int deff = deff_for(d);
+    const int CH = chunk_floats(deff), PPC = chunk_points(deff);
+
+    std::vector<int64_t> hoff(n_series + 1);
+    const bool off_dev = is_device_ptr(offsets);
+    if (off_dev) {
+        cudaError_t e = cudaMemcpy(hoff.data(), offsets, sizeof(int64_t) * (n_series + 1),
+                                   cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            return cuda_error(e, "copy offsets");
+    } else {
+        memcpy(hoff.data(), offsets, sizeof(int64_t) * (n_series + 1));
+    }
+    if (hoff[0] < 0)
+        return set_error(KNN_ERR_INVALID, "offsets[0] < 0");
+    int max_len = 0;
+    for (int64_t i = 0; i < n_series; ++i) {
+        const int64_t L = hoff[i + 1] - hoff[i];
+        if (L < 1)
+            return set_error(KNN_ERR_INVALID, "series " + std::to_string(i) + " has length < 1");
+        if (L > 65536)
+            return set_error(KNN_ERR_UNSUPPORTED, "series longer than 65536 points");
+        max_len = std::max<int>(max_len, (int)L);
+    }
+    return db_build(series, hoff, (int)n_series, d, max_len, 0, st, out);
+}
+
+extern "C" knn_status knn_db_create_windows(const float *series, int64_t n, int32_t d,
+                                            int32_t m, int32_t stride, void *stream,
+                                            knn_db **out)
+{
+    if (!out)
+        return set_error(KNN_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!series)
+        return set_error(KNN_ERR_INVALID, "series is NULL");
+    if (d < 1 || d > 16)
+        return set_error(KNN_ERR_INVALID, "d must be in [1, 16]");
+    if (m < 1 || n < m || stride < 1)
+        return set_error(KNN_ERR_INVALID, "need 1 <= m <= n and stride >= 1");
+    if (m > 65536)
+        return set_error(KNN_ERR_UNSUPPORTED, "windows longer than 65536 points");
+    const int64_t N = (n - m) / stride + 1;
+    if (N > (int64_t)0x7fffffff)
+        return set_error(KNN_ERR_INVALID, "more than 2^31 - 1 windows");
+    std::vector<int64_t> hoff(N + 1);
+    for (int64_t i = 0; i < N; ++i)
+        hoff[i] = i * stride;
+    hoff[N] = n;
+    return db_build(series, hoff, (int)N, d, m, m, (cudaStream_t)stream, out);
 }
 
 extern "C" knn_status knn_db_destroy(knn_db *db)

@@ -312,8 +312,11 @@ void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st);
 // zero) and zero padding up to the chunk-padded size.  dp_lead: the chunk of
 // floats before each series (reserved by the caller's offsets) is filled
 // with KNN_DP_SENTINEL, the point the DP reads for negative indices.
+// fixed_len > 0: every series has that many points from src_off[s] (the
+// series may overlap: windows of one long series).
 void launch_repack(const float *src, const int64_t *src_off, const int *order, int nser, int d,
-                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st, bool dp_lead);
+                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st, bool dp_lead,
+                   int fixed_len = 0);
 // dst[q][id[c]] = src[q][c] for c < n (bucket order -> caller order).
 void launch_scatter_by_id(const float *src, const int *db_id, int n, int nq, int64_t src_stride,
                           float *dst, int64_t dst_stride, int out_sqrt, cudaStream_t st);

@@ -40,7 +40,8 @@ void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st)
 
 // One warp per series.
 __global__ void repack_kernel(const float *src, const int64_t *src_off, const int *order, int nser,
-                              int d, int deff, const int64_t *dst_off, float *dst, int lead)
+                              int d, int deff, const int64_t *dst_off, float *dst, int lead,
+                              int fixed_len)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -50,7 +51,7 @@ __global__ void repack_kernel(const float *src, const int64_t *src_off, const in
     for (int c = warp; c < nser; c += nw) {
         const int s = order ? order[c] : c;
         const int64_t b = src_off[s];
-        const int n = (int)(src_off[s + 1] - b);
+        const int n = fixed_len > 0 ? fixed_len : (int)(src_off[s + 1] - b);
         const int64_t total = (int64_t)((n + ppc - 1) / ppc) * chf;
         const float *sp = src + b * d;
         float *dp = dst + dst_off[c];
@@ -65,7 +66,8 @@ __global__ void repack_kernel(const float *src, const int64_t *src_off, const in
 }
 
 void launch_repack(const float *src, const int64_t *src_off, const int *order, int nser, int d,
-                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st, bool dp_lead)
+                   int deff, const int64_t *dst_off, float *dst, cudaStream_t st, bool dp_lead,
+                   int fixed_len)
 {
     if (nser <= 0)
         return;
@@ -73,7 +75,7 @@ void launch_repack(const float *src, const int64_t *src_off, const int *order, i
     if (blocks > 8192)
         blocks = 8192;
     repack_kernel<<<blocks, 256, 0, st>>>(src, src_off, order, nser, d, deff, dst_off, dst,
-                                          dp_lead ? chunk_floats(deff) : 0);
+                                          dp_lead ? chunk_floats(deff) : 0, fixed_len);
 }
 
 __global__ void scatter_kernel(const float *src, const int *db_id, int n, int64_t src_stride,

@@ -29,17 +29,15 @@ def walk_series(rng, n, d):
     return np.cumsum(rng.standard_normal((n, d)), axis=0).astype(np.float32)
 
 
-def check(kind, q, t, v, end, rtol):
-    """GPU value within rtol of the oracle's; the GPU's end is an end of a best
-    match (the oracle's, or one whose prefix of T already holds the optimum)."""
+TOL = {0: 1e-5, 1: 1e-6}   # relative, DTW / DK (values re-scored in FP64)
+
+
+def check(kind, q, t, v, end):
+    """GPU value within the tolerance of the oracle's (no absolute slack) and
+    the same end column (the smallest of equal best values)."""
     ov, oend = oracle.sub_distance(kind, q.astype(np.float64), t.astype(np.float64))
-    assert v == pytest.approx(ov, rel=rtol, abs=1e-4), (v, ov)
-    if end != oend:
-        pv, _ = oracle.sub_distance(kind, q.astype(np.float64), t[: end + 1].astype(np.float64))
-        assert pv == pytest.approx(ov, rel=rtol, abs=1e-4), (end, oend, pv, ov)
-        if oend < end:
-            # a smaller end of an equal value: the two must be an FP32 near-tie
-            assert 0 <= oend
+    assert v == pytest.approx(ov, rel=TOL[kind], abs=0), (v, ov)
+    assert end == oend, (end, oend, v, ov)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
@@ -61,9 +59,8 @@ def test_subseq_matches_oracle(kw, kind, d):
     q_off = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.int64)
     vals, ends = kw.subseq(cuda(q), cuda(q_off), cuda(t), distance=kind)
     vals, ends = vals.cpu().numpy(), ends.cpu().numpy()
-    rtol = 2e-4 if kind == 0 else 1e-5
     for i, x in enumerate(qs):
-        check(kind, x, t, float(vals[i]), int(ends[i]), rtol)
+        check(kind, x, t, float(vals[i]), int(ends[i]))
 
 
 @pytest.mark.parametrize("kind", [0, 1])
@@ -77,7 +74,7 @@ def test_subseq_eps_and_edges(kw, kind):
     for f, expect in ((2.0, True), (1.001, True), (0.5, False)):
         v, e = kw.subseq(q, q_off, t, distance=kind, eps=float(ov * f))
         if expect:
-            assert float(v[0]) == pytest.approx(ov, rel=2e-4) and int(e[0]) == oend
+            assert float(v[0]) == pytest.approx(ov, rel=TOL[kind], abs=0) and int(e[0]) == oend
         else:
             assert math.isinf(float(v[0])) and int(e[0]) == -1
     # host inputs give the same as device inputs
@@ -93,7 +90,70 @@ def test_subseq_eps_and_edges(kw, kind):
     for tt, qq in ((t[:1], q), (t, q[:1]), (t[:1], q[:1])):
         qo = np.array([0, len(qq)], dtype=np.int64)
         v, e = kw.subseq(qq, qo, tt, distance=kind)
-        check(kind, qq, tt, float(v[0]), int(e[0]), 2e-4)
+        check(kind, qq, tt, float(v[0]), int(e[0]))
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d,k", [(1, 5), (3, 16), (8, 2)])
+def test_subseq_k_best_ends(kw, kind, d, k):
+    """The k best ends against the oracle's: the same ends in the same order,
+    values within the tolerance."""
+    rng = np.random.default_rng(300 + 10 * d + kind)
+    t = walk_series(rng, 2500, d)
+    qs = []
+    for m in (1, 17, 64, 150):
+        a = int(rng.integers(0, 2500 - m))
+        qs.append((t[a:a + m] + 0.05 * rng.standard_normal((m, d))).astype(np.float32))
+    q = np.concatenate(qs)
+    q_off = np.concatenate([[0], np.cumsum([len(x) for x in qs])]).astype(np.int64)
+    vals, ends = kw.subseq(cuda(q), cuda(q_off), cuda(t), distance=kind, k=k)
+    vals, ends = vals.cpu().numpy(), ends.cpu().numpy()
+    assert vals.shape == (len(qs), k)
+    for i, x in enumerate(qs):
+        ov, oe = oracle.sub_ends(kind, x.astype(np.float64), t.astype(np.float64), k)
+        np.testing.assert_array_equal(ends[i], oe)
+        np.testing.assert_allclose(vals[i], ov, rtol=TOL[kind], atol=0)
+    # k = 1 of knn_subseq_k is knn_subseq
+    v1, e1 = kw.subseq(cuda(q), cuda(q_off), cuda(t), distance=kind)
+    np.testing.assert_array_equal(e1.cpu().numpy(), ends[:, 0])
+    np.testing.assert_array_equal(v1.cpu().numpy(), vals[:, 0])
+    with pytest.raises(kw.KnnError):
+        kw.subseq(cuda(q), cuda(q_off), cuda(t), distance=kind, k=17)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d,stride", [(1, 1), (3, 3), (16, 2)])
+def test_banded_subsequence_windows(kw, kind, d, stride):
+    """Banded subsequence search: the k best length-m windows of T under the
+    Sakoe-Chiba band, against the oracle's k-NN over the same windows written
+    out explicitly (exact ids in order, distances within tolerance), and the
+    eps form."""
+    rng = np.random.default_rng(400 + d + stride + 10 * kind)
+    n, m, k, band = 1500, 64, 6, 0.1
+    t = walk_series(rng, n, d)
+    qs = [(t[a:a + m] + 0.05 * rng.standard_normal((m, d))).astype(np.float32)
+          for a in rng.integers(0, n - m, 4)]
+    q = np.concatenate(qs)
+    q_off = np.arange(len(qs) + 1, dtype=np.int64) * m
+    starts = np.arange(0, n - m + 1, stride)
+    win = np.concatenate([t[a:a + m] for a in starts])
+    w_off = np.arange(len(starts) + 1, dtype=np.int64) * m
+    db = kw.KnnDB.windows(cuda(t), m, stride)
+    assert db.n == len(starts)
+    ids, dist = db.scan(cuda(q), q_off, k=k, band=band, distance=kind)
+    oids, odist = oracle.knn(win, w_off, q, q_off, band=float(np.float32(band)), kind=kind, k=k)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    np.testing.assert_allclose(dist.cpu().numpy(), odist, rtol=TOL[kind], atol=0)
+    eps = float(np.float32(odist[:, 3].max()))
+    ei, ed, ec = db.scan(cuda(q), q_off, k=0, eps=eps, eps_capacity=len(starts), band=band,
+                         distance=kind)
+    oi, od, oc = oracle.knn(win, w_off, q, q_off, band=float(np.float32(band)), kind=kind, k=0,
+                            eps=eps, cap=len(starts))
+    np.testing.assert_array_equal(ec.cpu().numpy(), oc)
+    for i in range(len(qs)):
+        c = int(oc[i])
+        assert set(ei.cpu().numpy()[i, :c].tolist()) == set(oi[i, :c].tolist())
+    db.close()
 
 
 def test_subseq_greedy_bound(kw):

@@ -525,6 +525,28 @@ def test_subsequence_equals_min_over_all_subsequences(kind):
         assert all(per_end[b] > bv * (1 + 1e-12) + 1e-12 for b in range(end))
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_subsequence_k_best_ends(kind):
+    """The k best ends: the per-end values of the brute force over every
+    subsequence, k smallest by (value, end); k = 1 is sub_distance's answer."""
+    rng = np.random.default_rng(17)
+    for trial in range(30):
+        d = int(rng.integers(1, 4))
+        m = int(rng.integers(1, 5))
+        n = int(rng.integers(1, 10))
+        s = rng.standard_normal((m, d))
+        t = rng.standard_normal((n, d))
+        _, per_end = _brute_sub(kind, s, t)
+        k = int(rng.integers(1, n + 3))
+        vals, ends = oracle.sub_ends(kind, s, t, k)
+        expect = sorted((per_end[b], b) for b in range(n))[:k]
+        for j, (ev, eb) in enumerate(expect):
+            assert math.isclose(vals[j], ev, rel_tol=1e-12, abs_tol=1e-12) and ends[j] == eb
+        assert all(ends[j] == -1 and math.isinf(vals[j]) for j in range(len(expect), k))
+        v1, e1 = oracle.sub_distance(kind, s, t)
+        assert math.isclose(vals[0], v1, rel_tol=1e-12, abs_tol=1e-12) and ends[0] == e1
+
+
 def test_subsequence_sparse_dk_matches_plain_within_eps():
     """Algorithm 3 with SUB = true visits only cells of cost <= eps: it returns
     the subsequence DK when that is <= eps and +inf otherwise, never another
