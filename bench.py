@@ -278,6 +278,40 @@ def check_knn(ids, dist, oids, odist, kind) -> dict:
             bool(np.array_equal(np.isfinite(dist), fin))}
 
 
+def sampled_eps_parity(w, kind, eps, ids, dist, counts, nq: int, n_others: int,
+                       seed: int = 0) -> dict:
+    """Full-size eps-NN check on sampled outputs: for each of the first nq
+    queries the oracle computes (FP64) every returned series' distance and
+    n_others random other series'; passes if the returned ones are within
+    eps and agree within the tolerance, and no sampled other series is
+    within eps (up to the tolerance at eps itself)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    N = int(w.db_off.shape[0] - 1)
+    band = float(np.float32(BAND))
+    worst, ok = 0.0, True
+    for qi in range(nq):
+        got = [int(x) for x in ids[qi][: int(counts[qi])]]
+        gs = set(got)
+        others = [int(x) for x in rng.choice(N, size=min(n_others, N), replace=False)
+                  if int(x) not in gs]
+        sel = got + others
+        pts = [w.series(i) for i in sel]
+        b_off = np.zeros(len(sel) + 1, dtype=np.int64)
+        np.cumsum([len(p) for p in pts], out=b_off[1:])
+        q = w.query(qi)
+        od = oracle.pairwise(q, np.array([0, q.shape[0]], dtype=np.int64), np.concatenate(pts),
+                             b_off, np.zeros(len(sel), dtype=np.int64),
+                             np.arange(len(sel), dtype=np.int64), band=band, kind=kind)
+        gd = np.asarray(dist[qi][: len(got)], dtype=np.float64)
+        rel = np.abs(gd - od[: len(got)]) / np.maximum(np.abs(od[: len(got)]), 1e-30)
+        worst = max(worst, float(rel.max()) if rel.size else 0.0)
+        ok &= bool(np.all(od[: len(got)] <= eps * (1 + TOL[kind])))
+        ok &= bool(np.all(od[len(got):] > eps * (1 - TOL[kind])))
+    return {"queries": nq, "others_per_query": n_others, "max_rel_err": worst,
+            "tol": TOL[kind], "pass": bool(ok and worst <= TOL[kind])}
+
+
 def sampled_parity(w, kind, ids, dist, nq: int, n_others: int, seed: int = 0) -> dict:
     """Full-size check on sampled outputs: for each of the first nq queries
     the oracle computes (FP64) the distance of every returned series and of
@@ -584,6 +618,80 @@ def run_gpu(args):
             "setup_s": setup_s,
         }
 
+    # the eps-NN form: eps = the 1st percentile of the FP32 distances of the
+    # batch's queries to a seeded sample of 10,000 series (knn_pairwise on
+    # the GPU, pooled over queries: the scan takes one eps); the result sets
+    # are large (about 1 % of the database on average)
+    eps_nn = {}
+    if rank == 0 and not args.no_eps:
+        rng = np.random.default_rng(123)
+        samp = rng.choice(N_SERIES, size=min(10_000, N_SERIES), replace=False)
+        s_pts = np.concatenate([w.series(int(i)) for i in samp])
+        s_off = np.zeros(len(samp) + 1, dtype=np.int64)
+        np.cumsum([w.series(int(i)).shape[0] for i in samp], out=s_off[1:])
+        s_dev, s_off_dev = torch.from_numpy(s_pts).cuda(), torch.from_numpy(s_off).cuda()
+        q_off_dev = torch.from_numpy(q_off).cuda()
+        cap = 1 << 16
+        for kind in kinds:
+            pa = torch.arange(nq, device="cuda").repeat_interleave(len(samp))
+            pb = torch.arange(len(samp), device="cuda").repeat(nq)
+            dd, _ = kw.pairwise(q_dev, q_off_dev, s_dev, s_off_dev, pa, pb, band=BAND,
+                                distance=kind)
+            flat = dd.float().flatten()
+            kth = max(1, int(0.01 * flat.numel()))
+            eps_all = float(np.float32(torch.kthvalue(flat.cpu(), kth).values.item()))
+            del dd, flat, pa, pb
+            oi = torch.empty((nq, cap), dtype=torch.int64, device="cuda")
+            od = torch.empty((nq, cap), dtype=torch.float32, device="cuda")
+            oc = torch.empty(nq, dtype=torch.int64, device="cuda")
+            dbs[kind].scan(q_dev, q_off_t, k=0, eps=eps_all, eps_capacity=cap, band=BAND,
+                           distance=kind, out=(oi, od, oc))
+            torch.cuda.synchronize()
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            n_eps = max(1, min(args.steps, 2))
+            for _ in range(n_eps):
+                _, _, _, st = dbs[kind].scan(q_dev, q_off_t, k=0, eps=eps_all, eps_capacity=cap,
+                                             band=BAND, distance=kind, out=(oi, od, oc),
+                                             stats=True)
+            c1.record(stream)
+            c1.synchronize()
+            cnt = oc.cpu().numpy()
+            rec = {"queries_per_s": nq * n_eps / (c0.elapsed_time(c1) / 1000.0),
+                   "eps": eps_all, "eps_rule": "1st percentile of the FP32 distances of "
+                   "the batch's queries to 10,000 sampled series (pooled)",
+                   "mean_results": float(cnt.mean()), "max_results": int(cnt.max()),
+                   "capacity": cap, "dp_calls_per_query": st["dp_calls"] / nq}
+            if not args.no_parity:
+                rec["parity"] = sampled_eps_parity(w, kind, eps_all, oi.cpu().numpy(),
+                                                   od.cpu().numpy(), cnt, 4, 96, seed=kind)
+            eps_nn[kname[kind]] = rec
+        del s_dev, s_off_dev
+    if rank == 0:
+        line["eps_nn"] = eps_nn
+
+    # the LB_Box stream for one query (Section 3 Eq. 1 against every series,
+    # the single-query streaming kernel): database bytes / time, against HBM
+    if rank == 0 and not args.no_eps:
+        hbm_gbs, _, peak_src = peaks()
+        db_bytes = int(w.db.nbytes)
+        qi = torch.from_numpy(w.query(0)).cuda()
+        dbs[kinds[0]].lb_box(qi, BAND, 0)
+        torch.cuda.synchronize()
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for i in range(3):
+            dbs[kinds[0]].lb_box(torch.from_numpy(w.query(i)).cuda(), BAND, 0)
+        l1.record(stream)
+        l1.synchronize()
+        ms_lb = l0.elapsed_time(l1) / 3
+        gbs = db_bytes / (ms_lb / 1000.0) / 1e9
+        line["lb_single_query_stream"] = {
+            "kernel": "lb_kernel (knn_lb_box: envelope, stream, scatter)",
+            "ms": ms_lb, "database_bytes": db_bytes, "achieved_gbs": gbs, "peak_gbs": hbm_gbs,
+            "frac": gbs / hbm_gbs, "peak_source": peak_src}
+
     # parity of the measured configuration against the oracle
     if rank == 0 and not args.no_parity:
         par = {}
@@ -840,6 +948,8 @@ def main():
     ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the comparators (plain GPU scan, greedy, untrained encoder)")
+    ap.add_argument("--no-eps", action="store_true",
+                    help="skip the eps-NN form and the single-query LB_Box stream")
     ap.add_argument("--no-parity", action="store_true",
                     help="skip the oracle checks of the measured results")
     from synthdata import LONG_SERIES

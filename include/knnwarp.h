@@ -440,6 +440,18 @@ KNN_API knn_status knn_encoder_embed(knn_encoder *enc, const float *series,
 /* Embed every database series (BF16, kept by the database) so that scans
  * with seed_mode = KNN_SEED_LEARNED can rank series by predicted distance. */
 KNN_API knn_status knn_encoder_attach(knn_db *db, knn_encoder *enc, void *stream);
+/* The learned proposal's scores as a scan computes them (a component, for
+ * verification): queries are embedded (BF16) and every database series is
+ * scored by ||e_q - e_c||^2 from the attached BF16 embeddings, the dot
+ * products on the tcgen05 tensor cores with FP32 accumulation.  For each
+ * query and each tile of 64 consecutive series of the database's
+ * length-sorted order (the caller's order when all series have one length)
+ * out_score [n_queries][ceil(n_series / 64)] receives the lowest score and
+ * out_series the caller's id of that series (the first on ties).  Outputs:
+ * device memory.  KNN_ERR_INVALID without an attached encoder. */
+KNN_API knn_status knn_encoder_scores(knn_db *db, const float *queries, const int64_t *q_offsets,
+                                      int32_t n_queries, float *out_score, int64_t *out_series,
+                                      void *stream);
 /* Read (get) and/or replace (set) the FP32 parameters, host arrays of
  * knn_encoder_num_params() floats in the layout W1 [5][16][64], b1, W2
  * [5][64][64], b2, W3 [5][64][64], b3, Wl [64][64] (in x out), bl. */

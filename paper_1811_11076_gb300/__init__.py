@@ -40,7 +40,7 @@ EXPORTS = ("knn_db_create", "knn_db_destroy", "knn_db_info", "knn_scan", "knn_sc
            "knn_last_error", "knn_version", "knn_autotune", "knn_set_dp_shape", "knn_get_dp_shape",
            "knn_dp_shapes", "knn_set_lb_tile", "knn_get_lb_tile", "knn_set_lb_cascade",
            "knn_get_lb_cascade", "knn_lb_seg", "knn_subseq", "knn_subseq_k", "knn_db_create_windows", "knn_subseq_greedy", "knn_pairwise_noalloc", "knn_encoder_num_params", "knn_encoder_create",
-           "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach",
+           "knn_encoder_destroy", "knn_encoder_train", "knn_encoder_embed", "knn_encoder_attach", "knn_encoder_scores",
            "knn_encoder_params", "knn_encoder_loss_grad", "knn_encoder_save", "knn_encoder_load")
 
 
@@ -136,6 +136,7 @@ def lib() -> C.CDLL:
                                     C.POINTER(TrainStats), vp]
     L.knn_encoder_embed.argtypes = [vp, vp, vp, C.c_int64, vp, vp]
     L.knn_encoder_attach.argtypes = [vp, vp, vp]
+    L.knn_encoder_scores.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp]
     L.knn_encoder_params.argtypes = [vp, vp, vp]
     L.knn_encoder_loss_grad.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int64,
                                         C.POINTER(C.c_float), vp, vp]
@@ -405,6 +406,21 @@ class Encoder:
         _check(lib().knn_encoder_embed(self._h, _ptr(series), _ptr(offsets), n, _ptr(out),
                                        _stream(stream)))
         return out
+
+    @staticmethod
+    def scores(db: "KnnDB", queries, q_offsets, stream=None):
+        """Tile-best proposal scores of the encoder attached to db (tensor
+        cores): ([nq][tiles] float32, [nq][tiles] int64 series ids)."""
+        import torch
+        queries = _f32(queries)
+        q_offsets = _i64(q_offsets)
+        nq = int(q_offsets.shape[0] - 1)
+        tiles = (db.n + 63) // 64
+        sc = torch.empty((nq, tiles), dtype=torch.float32, device="cuda")
+        ids = torch.empty((nq, tiles), dtype=torch.int64, device="cuda")
+        _check(lib().knn_encoder_scores(db.handle, _ptr(queries), _ptr(q_offsets), nq, _ptr(sc),
+                                        _ptr(ids), _stream(stream)))
+        return sc, ids
 
     def attach(self, db: "KnnDB", stream=None):
         _check(lib().knn_encoder_attach(db.handle, self._h, _stream(stream)))

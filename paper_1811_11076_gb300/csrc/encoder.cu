@@ -397,94 +397,6 @@ __global__ void emb_to_bf16_kernel(const float *e, const int *dst_index, int B,
         norm_out[dst] = part[0] + part[1];
 }
 
-// Predicted distance ||e_q - e_c||^2 = |e_q|^2 + |e_c|^2 - 2 e_q.e_c for a
-// query tile (64) x series tile (64); the dot products on the tensor cores.
-// With tile_idx non-null only the lowest score of each 64-series tile and
-// its series are written per query ([nq][stride] with stride >= tiles).
-__global__ void __launch_bounds__(128) score_kernel(const __nv_bfloat16 *eq, const float *nq2,
-                                                    int nq, const __nv_bfloat16 *ec,
-                                                    const float *nc2, int n, float *score,
-                                                    int *tile_idx, int64_t stride)
-{
-    constexpr int S = ENC_E + 8;
-    __shared__ __align__(16) __nv_bfloat16 Qs[64 * S];
-    __shared__ __align__(16) __nv_bfloat16 Cs[64 * S];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t4 = lane & 3;
-    const int q0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
-    for (int i = tid; i < 64 * ENC_E / 2; i += blockDim.x) {
-        const int r = (2 * i) / ENC_E, k = (2 * i) % ENC_E;
-        uint32_t vq = 0, vc = 0;
-        if (q0 + r < nq)
-            vq = ld32(eq + (size_t)(q0 + r) * ENC_E + k);
-        if (c0 + r < n)
-            vc = ld32(ec + (size_t)(c0 + r) * ENC_E + k);
-        *reinterpret_cast<uint32_t *>(&Qs[r * S + k]) = vq;
-        *reinterpret_cast<uint32_t *>(&Cs[r * S + k]) = vc;
-    }
-    __syncthreads();
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            acc[nt][q] = 0.f;
-    const int r0 = warp * 16 + g;
-#pragma unroll
-    for (int ks = 0; ks < ENC_E / 16; ++ks) {
-        uint32_t af[4];
-        af[0] = ld32(&Qs[r0 * S + ks * 16 + 2 * t4]);
-        af[1] = ld32(&Qs[(r0 + 8) * S + ks * 16 + 2 * t4]);
-        af[2] = ld32(&Qs[r0 * S + ks * 16 + 2 * t4 + 8]);
-        af[3] = ld32(&Qs[(r0 + 8) * S + ks * 16 + 2 * t4 + 8]);
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            uint32_t bf[2];
-            bf[0] = ld32(&Cs[(nt * 8 + g) * S + ks * 16 + 2 * t4]);
-            bf[1] = ld32(&Cs[(nt * 8 + g) * S + ks * 16 + 2 * t4 + 8]);
-            mma_16816(acc[nt], af, bf);
-        }
-    }
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int q = q0 + r0 + 8 * half;
-        const float qn = q < nq ? nq2[q] : 0.f;
-        float best = KNN_INF;
-        int bidx = -1;
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int c = c0 + nt * 8 + 2 * t4 + j;
-                if (c < n && q < nq) {
-                    const float v = fmaxf(qn + nc2[c] - 2.f * acc[nt][2 * half + j], 0.f);
-                    if (!tile_idx)
-                        score[(int64_t)q * stride + c] = v;
-                    else if (v < best) {
-                        best = v;
-                        bidx = c;
-                    }
-                }
-            }
-        if (tile_idx) {
-            // minimum over the 4 lanes that hold this row's 64 columns
-#pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {
-                const float ob = __shfl_xor_sync(KNN_FULL_MASK, best, o);
-                const int oi = __shfl_xor_sync(KNN_FULL_MASK, bidx, o);
-                if (ob < best || (ob == best && oi >= 0 && (bidx < 0 || oi < bidx))) {
-                    best = ob;
-                    bidx = oi;
-                }
-            }
-            if (t4 == 0 && q < nq) {
-                score[(int64_t)q * stride + blockIdx.x] = best;
-                tile_idx[(int64_t)q * stride + blockIdx.x] = bidx;
-            }
-        }
-    }
-}
-
 __global__ void pair_targets_kernel(const float *raw, const int *la, const int *lb,
                                     const int2 *items, int n, int kind, float *target)
 {
@@ -672,11 +584,10 @@ static void enc_backward(knn_encoder *enc, const int *pa, const int *pb, const f
 
 knn_status enc_score(knn_encoder *enc, const __nv_bfloat16 *eq, const float *nq2, int nq,
                      const __nv_bfloat16 *ec, const float *nc2, int n, float *score,
-                     int *tile_idx, int64_t stride, cudaStream_t st)
+                     int *tile_idx, int64_t stride, int *status, cudaStream_t st)
 {
     (void)enc;
-    dim3 grid((n + 63) / 64, (nq + 63) / 64);
-    score_kernel<<<grid, 128, 0, st>>>(eq, nq2, nq, ec, nc2, n, score, tile_idx, stride);
+    launch_score_tc(eq, nq2, nq, ec, nc2, n, score, tile_idx, stride, status, st);
     return KNN_OK;
 }
 
@@ -700,7 +611,7 @@ void enc_init_attributes()
 // series of the database: score[q][c] = ||e_q - e_c||^2 (bucket order).
 knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, const int *q_len,
                            int nq, int max_m, void *qemb_v, float *qnorm, float *scores,
-                           int *tile_idx, cudaStream_t st)
+                           int *tile_idx, int *status, cudaStream_t st)
 {
     __nv_bfloat16 *qemb = static_cast<__nv_bfloat16 *>(qemb_v);
     knn_encoder *enc = db->enc;
@@ -710,7 +621,7 @@ knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, 
         return s;
     enc_emb_bf16(enc->e.as<float>(), nullptr, nq, qemb, qnorm, st);
     return enc_score(enc, qemb, qnorm, nq, db->emb.as<__nv_bfloat16>(), db->emb_norm.as<float>(),
-                     db->N, scores, tile_idx, (db->N + 63) / 64, st);
+                     db->N, scores, tile_idx, (db->N + 63) / 64, status, st);
 }
 
 }  // namespace knn
@@ -1166,6 +1077,94 @@ extern "C" knn_status knn_encoder_train(knn_encoder *enc, knn_db *db, int64_t n_
         stats->pairs = (int64_t)keep.size();
         stats->steps = steps;
     }
+    return KNN_OK;
+}
+
+// caller ids of the winners of each (query, tile): tile_idx is in the
+// database's length-sorted order
+__global__ void score_ids_kernel(const float *score, const int *tile_idx, const int *db_id,
+                                 int64_t total, float *out_score, int64_t *out_series)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = tile_idx[i];
+        out_score[i] = c >= 0 ? score[i] : KNN_INF;
+        out_series[i] = c >= 0 ? (int64_t)db_id[c] : -1;
+    }
+}
+
+extern "C" knn_status knn_encoder_scores(knn_db *db, const float *queries,
+                                         const int64_t *q_offsets, int32_t n_queries,
+                                         float *out_score, int64_t *out_series, void *stream)
+{
+    if (!db || !queries || !q_offsets || !out_score || !out_series)
+        return set_error(KNN_ERR_INVALID, "NULL argument");
+    if (!db->enc)
+        return set_error(KNN_ERR_INVALID, "no encoder attached to the database");
+    if (n_queries < 1)
+        return set_error(KNN_ERR_INVALID, "n_queries must be >= 1");
+    if (!is_device_ptr(out_score) || !is_device_ptr(out_series))
+        return set_error(KNN_ERR_INVALID, "outputs must be device memory");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> hq(n_queries + 1);
+    if (is_device_ptr(q_offsets))
+        cudaMemcpy(hq.data(), q_offsets, 8 * (n_queries + 1), cudaMemcpyDeviceToHost);
+    else
+        std::copy(q_offsets, q_offsets + n_queries + 1, hq.begin());
+    const int CH = chunk_floats(db->deff), PPC = chunk_points(db->deff);
+    std::vector<int64_t> rel(n_queries + 1), qoff(n_queries);
+    std::vector<int> len(n_queries);
+    int64_t qfloats = 0;
+    int max_m = 1;
+    for (int i = 0; i < n_queries; ++i) {
+        const int64_t m = hq[i + 1] - hq[i];
+        if (m < 1 || m > 65536)
+            return set_error(KNN_ERR_INVALID, "query lengths must be in [1, 65536]");
+        len[i] = (int)m;
+        max_m = std::max(max_m, (int)m);
+        qfloats += CH;  // leading chunk, as in the scan's layout
+        qoff[i] = qfloats;
+        qfloats += (m + PPC - 1) / PPC * CH;
+    }
+    for (int i = 0; i <= n_queries; ++i)
+        rel[i] = hq[i] - hq[0];
+    const int64_t tiles = (db->N + 63) / 64;
+    const int64_t npts = hq[n_queries] - hq[0];
+    DevBuf qraw, src_off, qbuf, qo, ql, qemb, qnorm, scores, idx, status;
+    knn_status s;
+    if ((s = qraw.ensure(sizeof(float) * npts * db->d)) || (s = src_off.ensure(8 * (n_queries + 1))) ||
+        (s = qbuf.ensure(sizeof(float) * qfloats)) || (s = qo.ensure(8 * n_queries)) ||
+        (s = ql.ensure(4 * n_queries)) || (s = qemb.ensure(2 * 64 * n_queries)) ||
+        (s = qnorm.ensure(4 * n_queries)) || (s = scores.ensure(4 * n_queries * tiles)) ||
+        (s = idx.ensure(4 * n_queries * tiles)) || (s = status.ensure(sizeof(int))))
+        return s;
+    const float *src = queries + hq[0] * db->d;
+    cudaMemcpyAsync(qraw.p, src, sizeof(float) * npts * db->d,
+                    is_device_ptr(queries) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(src_off.p, rel.data(), 8 * (n_queries + 1), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(qo.p, qoff.data(), 8 * n_queries, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ql.p, len.data(), 4 * n_queries, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(status.p, 0, sizeof(int), st);
+    launch_repack(qraw.as<float>(), src_off.as<int64_t>(), nullptr, n_queries, db->d, db->deff,
+                  qo.as<int64_t>(), qbuf.as<float>(), st, true);
+    if ((s = enc_work(db->enc, n_queries, max_m)))
+        return s;
+    if ((s = enc_scan_scores(db, qbuf.as<float>(), qo.as<int64_t>(), ql.as<int>(), n_queries,
+                             max_m, qemb.p, qnorm.as<float>(), scores.as<float>(), idx.as<int>(),
+                             status.as<int>(), st)))
+        return s;
+    const int64_t total = (int64_t)n_queries * tiles;
+    score_ids_kernel<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(
+        scores.as<float>(), idx.as<int>(), db->id.as<int>(), total, out_score, out_series);
+    int hs = 0;
+    cudaMemcpyAsync(&hs, status.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "encoder scores");
+    if (hs & KNN_DEV_TIMEOUT)
+        return set_error(KNN_ERR_TIMEOUT, "a device wait gave up");
     return KNN_OK;
 }
 

@@ -11,13 +11,16 @@
 //   linear 64 -> 64 -> embedding e [64]
 // Predicted distance of two series: ||e_a - e_b||^2.
 //
-// Arithmetic: BF16 operands on the tensor cores (mma.sync m16n8k16, FP32
-// accumulation) for the convolutions and their gradients; the input and
-// every convolution output are rounded to BF16 once; pooling, the linear
-// layer, the loss and Adam are FP32.  FP32 master weights.
+// Arithmetic: BF16 operands on the tensor cores with FP32 accumulation: the
+// convolutions and their gradients (mma.sync m16n8k16), the query x series
+// scores of a scan (tcgen05.mma with the accumulator in tensor memory,
+// score_tc.cu); the input and every convolution output are rounded to BF16
+// once; pooling, the linear layer, the loss and Adam are FP32.  FP32 master
+// weights.
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace knn {
@@ -37,5 +40,11 @@ constexpr int ENC_OFF_B3 = ENC_OFF_W3 + ENC_K * ENC_C * ENC_C;
 constexpr int ENC_OFF_WL = ENC_OFF_B3 + ENC_C;                  // [64 in][64 out]
 constexpr int ENC_OFF_BL = ENC_OFF_WL + ENC_C * ENC_E;
 constexpr int ENC_NPARAM = ENC_OFF_BL + ENC_E;
+
+// Lowest predicted distance of each 64-series tile per query and its series
+// ([nq][stride] each), on the tcgen05 tensor cores (score_tc.cu).
+void launch_score_tc(const __nv_bfloat16 *eq, const float *nq2, int nq, const __nv_bfloat16 *ec,
+                     const float *nc2, int n, float *score, int *tile_idx, int64_t stride,
+                     int *status, cudaStream_t st);
 
 }  // namespace knn

@@ -100,7 +100,7 @@ knn_status enc_work(knn_encoder *enc, int B, int L);
 // ([nq][ceil(N/64)], with the series in tile_idx).
 knn_status enc_scan_scores(knn_db *db, const float *qbuf, const int64_t *q_off, const int *q_len,
                            int nq, int max_m, void *qemb, float *qnorm, float *scores,
-                           int *tile_idx, cudaStream_t st);
+                           int *tile_idx, int *status, cudaStream_t st);
 }
 
 struct knn_db {

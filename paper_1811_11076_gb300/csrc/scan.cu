@@ -396,7 +396,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     if (pl.learned) {
         enc_scan_scores(db, ws.qbuf.as<float>(), ws.q_off.as<int64_t>(), ws.q_len.as<int>(), nq,
                         pl.max_m, ws.qemb.p, ws.qnorm.as<float>(), ws.scores.as<float>(),
-                        ws.sel.as<int>(), st);
+                        ws.sel.as<int>(), &ctrl->status, st);
         const int tiles = (db->N + 63) / 64;
         SelArgs sa{};
         sa.score = ws.scores.as<float>();

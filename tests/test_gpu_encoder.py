@@ -89,7 +89,8 @@ def test_training_and_learned_scan(kw, kind):
     """Training lowers the loss; the learned scan equals the oracle; and against
     the method without the learned proposal it does less work at identical
     results.  (Proposal recall of the trained and untrained encoders is
-    printed: on this data a random-feature encoder already ranks about as well.)"""
+    printed: on this small d = 3 set a random-feature encoder ranks about as
+    well; the d = 16 test below shows what training buys.)"""
     w = make_workload(n_series=4000, n_queries=24, d=3, length=96, n_classes=10, seed=21)
     db = kw.KnnDB(cuda(w.db), w.db_off)
     band, k = 0.1, 5
@@ -141,4 +142,76 @@ def test_training_and_learned_scan(kw, kind):
     # LB_Box-ordered proposals need every bound in full first; the learned
     # threshold exists before the stream, which abandons early
     assert L["lb_points"] < st["lb"]["lb_points"]
+    db.close()
+
+
+def test_training_improves_proposal_recall_at_d16(kw):
+    """What training buys on the d = 16 workload (a prefix of its database):
+    the trained encoder's S nearest embeddings hold more of the exact k
+    nearest series than those of untrained encoders (two initialisations),
+    at S = k and S = 2k; and the learned scan with the trained encoder does
+    no more LB_Box work than with an untrained one, at identical results."""
+    from synthdata import WORKLOADS
+    kwg = dict(WORKLOADS["highdim_d16_n500k_L512"], n_series=20000, n_queries=32)
+    w = make_workload(**kwg)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    k, band = 50, 0.1
+    ids, dist = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kw.DTW, seed=kw.SEED_LB)
+    top = ids.cpu().numpy()
+
+    def rec(enc, S):
+        eq = enc.embed(cuda(w.q), cuda(w.q_off)).cpu().numpy()
+        ed = enc.embed(cuda(w.db), cuda(w.db_off)).cpu().numpy()
+        return recall_at(eq, ed, top, S)
+
+    trained = kw.Encoder(16, seed=1)
+    tr = trained.train(db, 100000, epochs=6, batch_pairs=512, lr=2e-3, distance=kw.DTW,
+                       band=band)
+    assert tr["final_loss"] < 0.1 * tr["first_loss"], tr
+    for S in (k, 2 * k):
+        r_tr = rec(trained, S)
+        r_un = max(rec(kw.Encoder(16, seed=s), S) for s in (1, 2))
+        print("RECALL@", S, "trained", r_tr, "untrained (best of 2)", r_un)
+        assert r_tr > r_un + 0.02, (S, r_tr, r_un)
+    work = {}
+    for label, enc in (("trained", trained), ("untrained", kw.Encoder(16, seed=1))):
+        enc.attach(db)
+        i2, d2, st = db.scan(cuda(w.q), w.q_off, k=k, band=band, distance=kw.DTW,
+                             seed=kw.SEED_LEARNED, seed_count=k, stats=True)
+        np.testing.assert_array_equal(i2.cpu().numpy(), top)
+        np.testing.assert_array_equal(d2.cpu().numpy(), dist.cpu().numpy())
+        work[label] = st["lb_points"] + st["lb_segments"]
+    assert work["trained"] <= work["untrained"], work
+    db.close()
+
+
+@pytest.mark.parametrize("d", [3, 16])
+def test_tensor_core_proposal_scores(kw, d):
+    """The tcgen05 score kernel (tile-best ||e_q - e_c||^2 per query and
+    64-series tile) against FP64 scores of the same BF16 embeddings: 150
+    queries (a full and a partial 128-query tile) and 1,000 series (ragged
+    128- and 64-series tiles).  The reported score is the tile minimum within
+    FP32 accumulation error, and the reported series attains it."""
+    from oracle.encoder import round_bf16
+    w = make_workload(n_series=1000, n_queries=150, d=d, length=48, n_classes=6, seed=31 + d)
+    db = kw.KnnDB(cuda(w.db), w.db_off)
+    enc = kw.Encoder(d, seed=4)
+    enc.attach(db)
+    sc, ser = kw.Encoder.scores(db, cuda(w.q), cuda(w.q_off))
+    sc, ser = sc.cpu().numpy().astype(np.float64), ser.cpu().numpy()
+    eq = round_bf16(enc.embed(cuda(w.q), cuda(w.q_off)).cpu().numpy())
+    ed = round_bf16(enc.embed(cuda(w.db), cuda(w.db_off)).cpu().numpy())
+    qn, cn = (eq ** 2).sum(1), (ed ** 2).sum(1)
+    pred = np.maximum(qn[:, None] + cn[None, :] - 2.0 * eq @ ed.T, 0.0)
+    tiles = (1000 + 63) // 64
+    assert sc.shape == (150, tiles)
+    for t in range(tiles):
+        blk = pred[:, 64 * t: 64 * (t + 1)]
+        ref = blk.min(axis=1)
+        scale = 1e-5 * (qn + cn[64 * t: 64 * (t + 1)].max())
+        assert np.all(np.abs(sc[:, t] - ref) <= scale), t
+        chosen = pred[np.arange(150), ser[:, t]]
+        assert np.all((ser[:, t] >= 64 * t) & (ser[:, t] < min(1000, 64 * (t + 1))))
+        assert np.all(chosen <= ref + 2 * scale), t
+    enc.close()
     db.close()
