@@ -385,9 +385,10 @@ def run_gpu(args):
         dbs[kind] = kw.KnnDB(db_dev, w.db_off)
         if args.seed == "learned":
             enc = kw.Encoder(D, seed=11 + kind)
-            train_info[kname[kind]] = enc.train(
-                dbs[kind], TRAIN_PAIRS, epochs=3, batch_pairs=2048, lr=2e-3, distance=kind,
-                band=BAND, seed=5 + kind)
+            if args.train_pairs > 0:
+                train_info[kname[kind]] = enc.train(
+                    dbs[kind], args.train_pairs, epochs=3, batch_pairs=2048, lr=2e-3,
+                    distance=kind, band=BAND, seed=5 + kind)
             enc.attach(dbs[kind])
             encoders[kind] = enc
     del db_dev
@@ -800,11 +801,48 @@ def accuracy_table(kw, dims, lengths, n_series: int, n_queries: int, band: float
     return rows
 
 
+def lb_stream(args) -> dict:
+    """The LB_Box stream of one query (Section 3 Eq. 1 against every series;
+    the single-query streaming kernel via knn_lb_box) on the workload's
+    database: the call's time, and the database bytes it reads."""
+    import torch
+    import paper_1811_11076_gb300 as kw
+    select_workload(args.workload)
+    if args.series:
+        globals()["N_SERIES"] = args.series
+    w = workload(1)
+    db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
+    qs = [torch.from_numpy(w.query(i)).cuda() for i in range(8)]
+    for form in (0, 1):
+        db.lb_box(qs[0], BAND, form)
+    torch.cuda.synchronize()
+    out = {}
+    for form in (0, 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for q in qs:
+            db.lb_box(q, BAND, form)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / len(qs)
+        out[f"form{form}"] = {"ms_per_call": ms, "gbs_per_call": w.db.nbytes / ms / 1e6}
+    db.close()
+    hbm, _, src = peaks()
+    return {"workload": WORKLOAD, "n_series": N_SERIES, "database_bytes": int(w.db.nbytes),
+            "calls": out, "peak_gbs": hbm, "peak_source": src,
+            "note": "call time includes the query upload, envelope and scatter kernels"}
+
+
 def run_experiment(args):
     """Tightness sweep (the Theorem's trend) or 1-NN accuracy, one JSON line."""
     import paper_1811_11076_gb300 as kw
     kw.lib()
     t0 = time.perf_counter()
+    if args.experiment == "lbstream":
+        line = {"experiment": "lbstream", **lb_stream(args)}
+        line["seconds"] = time.perf_counter() - t0
+        print(json.dumps(line), flush=True)
+        return 0
     if args.experiment == "tightness":
         rows = {data: tightness_table(kw, (1, 2, 4, 8, 16),
                                       (32, 64, 128, 256, 512), 128, 0.1, data)
@@ -948,6 +986,8 @@ def main():
     ap.add_argument("--seed", default="learned", choices=["greedy", "lb", "none", "learned"])
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the comparators (plain GPU scan, greedy, untrained encoder)")
+    ap.add_argument("--train-pairs", type=int, default=TRAIN_PAIRS,
+                    help="pairs the encoder trains on (0: untrained, for profiling captures)")
     ap.add_argument("--no-eps", action="store_true",
                     help="skip the eps-NN form and the single-query LB_Box stream")
     ap.add_argument("--no-parity", action="store_true",
@@ -962,9 +1002,9 @@ def main():
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default="", help="P,G: fix the DP shape instead of tuning it")
-    ap.add_argument("--experiment", default="", choices=["", "tightness", "accuracy"],
-                    help="instead of the throughput line: the LB_Box tightness sweep or the "
-                         "1-NN accuracy of DTW and DK")
+    ap.add_argument("--experiment", default="", choices=["", "tightness", "accuracy", "lbstream"],
+                    help="instead of the throughput line: the LB_Box tightness sweep, the "
+                         "1-NN accuracy of DTW and DK, or the single-query LB_Box stream alone")
     ap.add_argument("--lb-qtile", type=int, default=0, choices=[0, 4, 8, 16],
                     help="queries per LB_Box pass (0: 16, or tuned)")
     ap.add_argument("--lb-compaction", type=int, default=0, choices=[0, 1, 2],

@@ -221,22 +221,26 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
             if (feasible) {
                 const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
                 const int nch = (n + PPC - 1) / PPC;
-                // two chunks per lane per iteration: six to eight independent
-                // 16-byte loads in flight per lane before any arithmetic
-                for (int ch0 = lane; ch0 < nch; ch0 += 64) {
-                    const int ch1 = ch0 + 32;
-                    float4 xa[F4], xb[F4];
+                // UNR chunks per lane per iteration: 16 independent 16-byte
+                // loads in flight per lane before any arithmetic
+                constexpr int UNR = F4 <= 2 ? 8 : 4;
+                for (int ch0 = lane; ch0 < nch; ch0 += 32 * UNR) {
+                    float4 xv[UNR][F4];
 #pragma unroll
-                    for (int f = 0; f < F4; ++f)
-                        xa[f] = __ldg(x4 + ch0 * F4 + f);
-                    if (ch1 < nch) {
+                    for (int u = 0; u < UNR; ++u) {
+                        const int ch = ch0 + 32 * u;
+                        if (ch < nch) {
 #pragma unroll
-                        for (int f = 0; f < F4; ++f)
-                            xb[f] = __ldg(x4 + ch1 * F4 + f);
+                            for (int f = 0; f < F4; ++f)
+                                xv[u][f] = __ldg(x4 + ch * F4 + f);
+                        }
                     }
-                    lb_chunk<D, PPC, F4, FORM>(xa, lo_s, hi_s, ch0, n, acc);
-                    if (ch1 < nch)
-                        lb_chunk<D, PPC, F4, FORM>(xb, lo_s, hi_s, ch1, n, acc);
+#pragma unroll
+                    for (int u = 0; u < UNR; ++u) {
+                        const int ch = ch0 + 32 * u;
+                        if (ch < nch)
+                            lb_chunk<D, PPC, F4, FORM>(xv[u], lo_s, hi_s, ch, n, acc);
+                    }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -1056,7 +1060,13 @@ static void lb_launch_d(const LbArgs &a, int form, int n_sm, cudaStream_t st)
     auto kern = form == 0 ? lb_kernel<D, 0> : lb_kernel<D, 1>;
     const int nser = a.c_end - a.c_begin;
     const int ntiles = (nser + 31) / 32;
-    int want = (n_sm * 4 + a.nq - 1) / a.nq;
+    // one full wave of the CTAs that fit with this envelope size (the kernel
+    // loops over the tiles)
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, LB_THREADS, smem);
+    if (resident < 1)
+        resident = 1;
+    int want = (n_sm * resident + a.nq - 1) / a.nq;
     int maxx = (ntiles + LB_WARPS - 1) / LB_WARPS;
     int bx = want < maxx ? want : maxx;
     if (bx < 1)
