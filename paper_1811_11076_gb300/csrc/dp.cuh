@@ -50,6 +50,9 @@
 namespace knn {
 
 constexpr int DP_THREADS = 128;
+// WIN kernels: steps between the global load of a window piece and its store
+// into shared memory (the load's latency hides behind that many steps)
+constexpr int DP_WIN_AHEAD = 2;
 // Point idx of a series, clamped to [-1, last]: index -1 is the sentinel
 // point stored in the chunk before every series and query the DP reads.
 template <int D>
@@ -85,6 +88,18 @@ __device__ __forceinline__ float dp_cost(const float (&a)[D], const float (&b)[D
         return sqdist_acc_p2<D>(a, b, init);
     else
         return sqdist_acc<D>(a, b, init);
+}
+
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned),
+// and the wait for every copy this thread has issued.
+__device__ __forceinline__ void cp_async16(float *dst_smem, const float *src)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Rows of the shared-memory window of one lane group (WIN kernels): the
@@ -144,8 +159,12 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
     const int wp_mask = W / P - 1;
     float *qwin = dwin + (size_t)(((threadIdx.x >> 5) * (32 / G) + (lane / G)) * 2 * W) * RS;
     float *xwin = qwin + (size_t)W * RS;
-    // WIN: the pieces of the next two steps, loaded two steps ahead
-    float4 pf0 = make_float4(0.f, 0.f, 0.f, 0.f), pf1 = pf0;
+    // WIN: the pieces of the next DP_WIN_AHEAD steps, loaded that many steps
+    // ahead of their use
+    float4 pf[DP_WIN_AHEAD];
+#pragma unroll
+    for (int t = 0; t < DP_WIN_AHEAD; ++t)
+        pf[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool win_loader = WIN && lam < 2 * (D / 4);
 
     float qw[U][D], xw[U][D];
@@ -250,24 +269,27 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                         }
                         if constexpr (WIN) {
                             // the (G-1)P rows and columns before the first step's
-                            // newest, in float4 pieces spread over the group
+                            // newest, in float4 pieces spread over the group, copied
+                            // global -> shared asynchronously (no registers, all
+                            // copies in flight at once); the step loop's __syncwarp
+                            // publishes them to the group after the wait below
                             const int h0 = lo / 2, hT = lo / 2 + P * (G - 1);
                             const int nf = (G - 1) * P * (D / 4);
                             for (int t = lam; t < nf; t += G) {
                                 const int k = t / (D / 4), c = t - k * (D / 4);
                                 const int rq = s0 - h0 - (G - 1) * P + k;
                                 const int cx = s0 + h0 + P + k;
-                                const float4 vq = __ldg(reinterpret_cast<const float4 *>(
-                                    qp + (int64_t)clampi(rq, -1, m - 1) * D) + c);
-                                const float4 vx = __ldg(reinterpret_cast<const float4 *>(
-                                    xp + (int64_t)clampi(cx, -1, n - 1) * D) + c);
-                                reinterpret_cast<float4 *>(qwin + dp_win_slot<P>(rq, wp_mask) * RS)[c] = vq;
-                                reinterpret_cast<float4 *>(xwin + dp_win_slot<P>(cx, wp_mask) * RS)[c] = vx;
+                                cp_async16(qwin + dp_win_slot<P>(rq, wp_mask) * RS + 4 * c,
+                                           qp + (int64_t)clampi(rq, -1, m - 1) * D + 4 * c);
+                                cp_async16(xwin + dp_win_slot<P>(cx, wp_mask) * RS + 4 * c,
+                                           xp + (int64_t)clampi(cx, -1, n - 1) * D + 4 * c);
                             }
                             if (win_loader) {
-                                pf0 = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s0);
-                                pf1 = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s0 + 1);
+#pragma unroll
+                                for (int t = 0; t < DP_WIN_AHEAD; ++t)
+                                    pf[t] = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s0 + t);
                             }
+                            cp_async_wait_all();
                         }
                         active = true;
                         st_calls += (lam == 0);
@@ -278,6 +300,11 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
         }
         if (__all_sync(KNN_FULL_MASK, done))
             break;
+        // the threshold of this block's abandon test, read now so that the
+        // load's latency hides behind the block's steps: thresholds only fall,
+        // so a value one block old is still a valid (looser) bound, and the
+        // top-k insert keeps the exact k best whatever it is offered
+        const float thr_blk = (active && !a.out_pair) ? ld_volatile_f32(a.thr + qi) : KNN_INF;
 
         // ---- U steps of the wavefront ----------------------------------------
 #pragma unroll
@@ -293,9 +320,11 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                     const int c = isx ? lam - D / 4 : lam;
                     float *dst = isx ? xwin + dp_win_slot<P>(s + hT + P, wp_mask) * RS
                                      : qwin + dp_win_slot<P>(s - h0, wp_mask) * RS;
-                    reinterpret_cast<float4 *>(dst)[c] = pf0;
-                    pf0 = pf1;
-                    pf1 = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s + 2);
+                    reinterpret_cast<float4 *>(dst)[c] = pf[0];
+#pragma unroll
+                    for (int t = 0; t + 1 < DP_WIN_AHEAD; ++t)
+                        pf[t] = pf[t + 1];
+                    pf[DP_WIN_AHEAD - 1] = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s + DP_WIN_AHEAD);
                 }
                 __syncwarp();
                 const float4 *qs =
@@ -352,8 +381,7 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
         for (int o = 1; o < G; o <<= 1)
             mn = fminf(mn, __shfl_xor_sync(KNN_FULL_MASK, mn, o));
         if (active) {
-            const float thr = a.out_pair ? KNN_INF : ld_volatile_f32(a.thr + qi);
-            const float lim = thr * a.mu_keep;
+            const float lim = thr_blk * a.mu_keep;
             const bool finished = (s0 - 1 == s_f);
             if (finished) {
                 if (lam == 0) {

@@ -425,6 +425,121 @@ __global__ void __launch_bounds__(LBP_THREADS) lb_pair_kernel(const PairLbArgs a
     flush_stat(a.stats, STAT_LB_POINTS, st_points);
 }
 
+// The same exact stage for point widths that are whole float4 vectors
+// (D = 4, 8, 16: one point per chunk, FPP float4 per point).  The group's 8
+// lanes read consecutive float4 of the series and of the envelope, so every
+// load instruction of a group covers 128 contiguous bytes (the chunk-per-lane
+// order above puts the lanes 16 D bytes apart and needs D/4 times the L1
+// wavefronts).  The sum form adds every element's squared gap; the max form
+// first joins the FPP lanes that hold one point (xor shuffles), then takes
+// the maximum over points.
+template <int D, int FORM>
+__global__ void __launch_bounds__(LBP_THREADS) lb_pair4_kernel(const PairLbArgs a)
+{
+    static_assert(D % 4 == 0 && D <= 32, "whole float4 points");
+    constexpr int FPP = D / 4;                 // float4 per point
+    constexpr int UNR = 4;                     // float4 per lane per round
+    constexpr int RF4 = LBP_GROUP * UNR;       // float4 per group per round
+    constexpr int GPW = 32 / LBP_GROUP;
+    const int lane = threadIdx.x & 31, grp = lane / LBP_GROUP, gl = lane % LBP_GROUP;
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int total = (int)min((int64_t)*a.cq_count, a.cq_cap);
+    unsigned long long st_pruned = 0, st_points = 0;
+    for (int base = warp * GPW; base < total; base += nwarps * GPW) {
+        const int idx = base + grp;
+        const bool valid = idx < total;
+        const int2 it = valid ? a.cq[idx] : make_int2(0, 0);
+        const int c = it.x, qb = it.y;
+        const int n = valid ? a.db_len[c] : 0;
+        const float lim = valid ? ld_volatile_f32(a.thr + qb) * a.mu_prune : -1.f;
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+        const float4 *lo4 = reinterpret_cast<const float4 *>(a.env_lo + (int64_t)qb * a.env_stride);
+        const float4 *hi4 = reinterpret_cast<const float4 *>(a.env_hi + (int64_t)qb * a.env_stride);
+        const int nf4 = n * FPP;
+        const int nf4_max = __reduce_max_sync(KNN_FULL_MASK, nf4);
+        float acc[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            acc[u] = 0.f;
+        float tot = 0.f;
+        bool alive = valid;
+        for (int r0 = 0, round = 0; r0 < nf4_max; r0 += RF4, ++round) {
+            float4 xv[UNR], lv[UNR], hv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int j = r0 + u * LBP_GROUP + gl;
+                if (alive && j < nf4) {
+                    xv[u] = __ldg(x4 + j);
+                    lv[u] = __ldg(lo4 + j);
+                    hv[u] = __ldg(hi4 + j);
+                    st_points += (j % FPP) == 0;
+                } else {
+                    // a zero element with a zero box: gap 0, adds nothing
+                    xv[u] = lv[u] = hv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const float ex = box_gap(xv[u].x, lv[u].x, hv[u].x);
+                const float ey = box_gap(xv[u].y, lv[u].y, hv[u].y);
+                const float ez = box_gap(xv[u].z, lv[u].z, hv[u].z);
+                const float ew = box_gap(xv[u].w, lv[u].w, hv[u].w);
+                if constexpr (FORM == 0) {
+                    float t = acc[u];
+                    t = __fmaf_rn(ex, ex, t);
+                    t = __fmaf_rn(ey, ey, t);
+                    t = __fmaf_rn(ez, ez, t);
+                    acc[u] = __fmaf_rn(ew, ew, t);
+                } else {
+                    float t = __fmaf_rn(ex, ex, 0.f);
+                    t = __fmaf_rn(ey, ey, t);
+                    t = __fmaf_rn(ez, ez, t);
+                    t = __fmaf_rn(ew, ew, t);
+#pragma unroll
+                    for (int o = 1; o < FPP; o <<= 1)
+                        t += __shfl_xor_sync(KNN_FULL_MASK, t, o);
+                    acc[u] = fmaxf(acc[u], t);
+                }
+            }
+            if ((round & 3) == 3 || r0 + RF4 >= nf4_max) {
+                tot = acc[0];
+#pragma unroll
+                for (int u = 1; u < UNR; ++u)
+                    tot = FORM == 0 ? tot + acc[u] : fmaxf(tot, acc[u]);
+#pragma unroll
+                for (int o = 1; o < LBP_GROUP; o <<= 1) {
+                    const float other = __shfl_xor_sync(KNN_FULL_MASK, tot, o);
+                    tot = FORM == 0 ? tot + other : fmaxf(tot, other);
+                }
+                alive = alive && tot <= lim;
+                if (!__any_sync(KNN_FULL_MASK, alive))
+                    break;
+            }
+        }
+        const bool keep = alive && gl == 0;
+        st_pruned += valid && gl == 0 && !alive;
+        const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
+        if (kb) {
+            int pos0 = 0;
+            if (lane == 0)
+                pos0 = atomicAdd(a.n_items, __popc(kb));
+            pos0 = __shfl_sync(KNN_FULL_MASK, pos0, 0);
+            if (keep) {
+                const int64_t pos = (int64_t)pos0 + __popc(kb & ((1u << lane) - 1u));
+                if (pos < a.capacity) {
+                    a.items[pos] = make_int2(c, qb);
+                    a.item_lb[pos] = tot;
+                } else {
+                    atomicOr(a.status, KNN_DEV_CAPACITY);
+                }
+            }
+        }
+    }
+    flush_stat(a.stats, STAT_LB_PRUNED, st_pruned);
+    flush_stat(a.stats, STAT_LB_POINTS, st_points);
+}
+
 }  // namespace
 
 void launch_seg_means(const float *data, const int64_t *off, const int *len, int N, int deff,
@@ -484,10 +599,17 @@ bool coarse_launch_d(const CoarseArgs &a, int form, int qt, int n_sm, cudaStream
 template <int D>
 void pair_launch_d(const PairLbArgs &a, int form, int n_sm, cudaStream_t st)
 {
-    if (form == 0)
-        lb_pair_kernel<D, 0><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
-    else
-        lb_pair_kernel<D, 1><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
+    if constexpr (D % 4 == 0) {
+        if (form == 0)
+            lb_pair4_kernel<D, 0><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
+        else
+            lb_pair4_kernel<D, 1><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
+    } else {
+        if (form == 0)
+            lb_pair_kernel<D, 0><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
+        else
+            lb_pair_kernel<D, 1><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
+    }
 }
 
 template <int D, int QT>

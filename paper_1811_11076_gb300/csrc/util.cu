@@ -38,26 +38,26 @@ void launch_fill_f32(float *p, float v, int64_t n, cudaStream_t st)
         fill_f32_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p, v, n);
 }
 
-// One warp per series.
+// One CTA per series (grid-stride over the series in x); when there are few
+// series, blockIdx.y splits each series' floats over gridDim.y CTAs.
 __global__ void repack_kernel(const float *src, const int64_t *src_off, const int *order, int nser,
                               int d, int deff, const int64_t *dst_off, float *dst, int lead,
                               int fixed_len)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ppc = chunk_floats(deff) / deff;  // host guarantees deff is a compiled width
     const int chf = chunk_floats(deff);
-    for (int c = warp; c < nser; c += nw) {
+    const int t0 = blockIdx.y * blockDim.x + threadIdx.x;
+    const int tstride = gridDim.y * blockDim.x;
+    for (int c = blockIdx.x; c < nser; c += gridDim.x) {
         const int s = order ? order[c] : c;
         const int64_t b = src_off[s];
         const int n = fixed_len > 0 ? fixed_len : (int)(src_off[s + 1] - b);
         const int64_t total = (int64_t)((n + ppc - 1) / ppc) * chf;
         const float *sp = src + b * d;
         float *dp = dst + dst_off[c];
-        for (int f = lane; f < lead; f += 32)
+        for (int f = t0; f < lead; f += tstride)
             dp[f - lead] = KNN_DP_SENTINEL;
-        for (int64_t f = lane; f < total; f += 32) {
+        for (int64_t f = t0; f < total; f += tstride) {
             const int64_t i = f / deff;
             const int j = (int)(f - i * deff);
             dp[f] = (i < n && j < d) ? sp[i * d + j] : 0.f;
@@ -71,11 +71,10 @@ void launch_repack(const float *src, const int64_t *src_off, const int *order, i
 {
     if (nser <= 0)
         return;
-    int blocks = (nser + 7) / 8;
-    if (blocks > 8192)
-        blocks = 8192;
-    repack_kernel<<<blocks, 256, 0, st>>>(src, src_off, order, nser, d, deff, dst_off, dst,
-                                          dp_lead ? chunk_floats(deff) : 0, fixed_len);
+    const int bx = nser < 8192 ? nser : 8192;
+    const int by = nser >= 1024 ? 1 : (1024 / nser < 64 ? 1024 / nser : 64);
+    repack_kernel<<<dim3(bx, by), 256, 0, st>>>(src, src_off, order, nser, d, deff, dst_off, dst,
+                                                dp_lead ? chunk_floats(deff) : 0, fixed_len);
 }
 
 __global__ void scatter_kernel(const float *src, const int *db_id, int n, int64_t src_stride,

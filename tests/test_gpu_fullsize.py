@@ -1,6 +1,7 @@
-"""Parity at the benchmark's full size: d=3, 100,000 series of length 256,
-1,000 queries scanned in one batch (the launch configuration bench.py times),
-sampled queries checked one by one against the FP64 oracle."""
+"""Parity at full size, in the launch configuration bench.py times (1,000
+queries scanned in one batch): the d = 16 workload (500,000 series of length
+512, k = 50, learned seeding) and the d = 3 one (100,000 x 256); sampled
+queries checked one by one against the FP64 oracle."""
 import os
 
 import numpy as np
@@ -44,3 +45,57 @@ def test_full_size_sampled(setup, kind, k, band, seed):
     assert np.all(np.diff(dist, axis=1) >= 0)
     assert np.all(np.isfinite(dist))
     assert all(len(set(r)) == k for r in ids)
+
+
+@pytest.fixture(scope="module")
+def setup16():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_11076_gb300 as kw
+    from paper_1811_11076_gb300 import build
+    from synthdata import WORKLOADS, make_workload
+    build.build()
+    w = make_workload(**WORKLOADS["highdim_d16_n500k_L512"])
+    db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
+    enc = kw.Encoder(16, seed=11)   # untrained: the proposal orders work only
+    enc.attach(db)
+    yield kw, w, db, torch.from_numpy(w.q).cuda()
+    enc.close()
+    db.close()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_full_size_d16(setup16, kind):
+    """The 500,000 x 512 x 16 database, 1,000 queries in one batch, k = 50,
+    band 10 %, learned seeding: one query's rows equal the oracle's exact scan
+    (ids and distances); for three more, every returned distance is the
+    oracle's and none of 192 random other series is closer than the 50-th."""
+    kw, w, db, q = setup16
+    k, band = 50, 0.1
+    tol = 1e-5 if kind == 0 else 1e-6
+    ids, dist = db.scan(q, w.q_off, k=k, band=band, distance=kind, seed=kw.SEED_LEARNED)
+    ids, dist = ids.cpu().numpy(), dist.cpu().numpy().astype(np.float64)
+    assert ids.shape == (1000, k)
+    assert np.all(np.isfinite(dist)) and np.all(np.diff(dist, axis=1) >= 0)
+    assert all(len(set(r)) == k for r in ids)
+    rng = np.random.default_rng(77 + kind)
+    sample = np.sort(rng.choice(1000, 4, replace=False))
+    fb = float(np.float32(band))
+    qi = int(sample[0])
+    oids, odist = oracle.knn(w.db, w.db_off, w.query(qi), np.array([0, 512]), band=fb,
+                             kind=kind, k=k, method=True, threads=os.cpu_count())
+    assert list(ids[qi]) == list(oids[0])
+    np.testing.assert_allclose(dist[qi], odist[0], rtol=tol)
+    N = w.db_off.shape[0] - 1
+    for qi in sample[1:]:
+        got = [int(x) for x in ids[qi]]
+        others = [int(x) for x in rng.choice(N, 192, replace=False) if int(x) not in set(got)]
+        sel = got + others
+        b = np.concatenate([w.series(i) for i in sel])
+        b_off = np.arange(len(sel) + 1, dtype=np.int64) * 512
+        od = oracle.pairwise(w.query(qi), np.array([0, 512]), b, b_off,
+                             np.zeros(len(sel), dtype=np.int64),
+                             np.arange(len(sel), dtype=np.int64), band=fb, kind=kind)
+        np.testing.assert_allclose(dist[qi], od[:k], rtol=tol)
+        assert np.all(od[k:] >= od[k - 1] * (1 - tol))
