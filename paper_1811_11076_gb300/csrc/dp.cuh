@@ -50,8 +50,8 @@
 namespace knn {
 
 constexpr int DP_THREADS = 128;
-// WIN kernels: steps between the global load of a window piece and its store
-// into shared memory (the load's latency hides behind that many steps)
+// WIN kernels: steps between the asynchronous copy of a window piece and its
+// first read (the copy's latency hides behind that many steps)
 constexpr int DP_WIN_AHEAD = 2;
 // Point idx of a series, clamped to [-1, last]: index -1 is the sentinel
 // point stored in the chunk before every series and query the DP reads.
@@ -101,14 +101,26 @@ __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+// Wait until at most N of this thread's committed groups are still pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-// Rows of the shared-memory window of one lane group (WIN kernels): the
-// newest row any lane reads and the G-1 strides of P below it, plus one, as
-// a power of two.
+// Rows of the shared-memory window of one lane group (WIN kernels), a power
+// of two: the (G-1)P + 1 rows the group's lanes read in one step, the
+// DP_WIN_AHEAD rows whose copies are in flight, and one more, so that a copy
+// issued in step s never lands on a row that a lane may still read in step
+// s - 1 (lanes of a warp meet only at each step's __syncwarp).
 __host__ __device__ constexpr int dp_win_rows(int G, int P)
 {
     int w = 1;
-    while (w < (G - 1) * P + 2)
+    while (w < (G - 1) * P + 2 + DP_WIN_AHEAD)
         w <<= 1;
     return w;
 }
@@ -123,24 +135,35 @@ __device__ __forceinline__ int dp_win_slot(int r, int wp_mask)
     static_assert((1 << LP) == P, "window path needs P a power of two");
     return (r & (P - 1)) * (wp_mask + 1) + ((r >> LP) & wp_mask);
 }
-// WIN kernels: the group's newest query row (s - h_0) and series column
-// (s + h_{G-1} + P) of step s come in 2*(D/4) float4 pieces, one per lane
-// lam < 2*(D/4) (G >= 8 and D <= 16, so a group has lanes enough).
-template <int D>
-__device__ __forceinline__ float4 dp_win_fetch(const float *qp, const float *xp, int m, int n,
-                                               int lam, int h0, int hT, int P, int s)
+// WIN kernels: the group's newest query row (t - h_0) and series column
+// (t + h_{G-1} + P) of step t come in 2*(D/4) float4 pieces, one per lane
+// lam < 2*(D/4) (G >= 8 and D <= 16, so a group has lanes enough), copied
+// global -> shared asynchronously into their window slots.
+template <int D, int P>
+__device__ __forceinline__ void dp_win_copy(float *qwin, float *xwin, int wp_mask,
+                                            const float *qp, const float *xp, int m, int n,
+                                            int lam, int h0, int hT, int t)
 {
-    constexpr int C = D / 4;
+    constexpr int C = D / 4, RS = D + 4;
     const bool isx = lam >= C;
     const int c = isx ? lam - C : lam;
-    const float *src = isx ? xp + (int64_t)clampi(s + hT + P, -1, n - 1) * D
-                           : qp + (int64_t)clampi(s - h0, -1, m - 1) * D;
-    return __ldg(reinterpret_cast<const float4 *>(src) + c);
+    const int idx = isx ? t + hT + P : t - h0;
+    float *dst = (isx ? xwin : qwin) + dp_win_slot<P>(idx, wp_mask) * RS + 4 * c;
+    const float *src = isx ? xp + (int64_t)clampi(idx, -1, n - 1) * D
+                           : qp + (int64_t)clampi(idx, -1, m - 1) * D;
+    cp_async16(dst, src + 4 * c);
 }
-// Dynamic shared memory of a WIN kernel CTA: 32P rows per array per warp.
+// Dynamic shared memory of a WIN kernel CTA: per warp, 32/G groups of two
+// windows of dp_win_rows(G, P) rows, the most over the group sizes 8, 16, 32
+// (one allocation per kernel whatever G a launch uses).
 __host__ __device__ constexpr size_t dp_win_bytes(int D, int P)
 {
-    return (size_t)(DP_THREADS / 32) * 2 * 32 * P * (D + 4) * sizeof(float);
+    size_t rows = 0;
+    for (int G = 8; G <= 32; G *= 2) {
+        const size_t r = (size_t)(32 / G) * dp_win_rows(G, P);
+        rows = r > rows ? r : rows;
+    }
+    return (size_t)(DP_THREADS / 32) * 2 * rows * (D + 4) * sizeof(float);
 }
 
 template <int D, int P, int KIND, bool WIN>
@@ -159,13 +182,9 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
     const int wp_mask = W / P - 1;
     float *qwin = dwin + (size_t)(((threadIdx.x >> 5) * (32 / G) + (lane / G)) * 2 * W) * RS;
     float *xwin = qwin + (size_t)W * RS;
-    // WIN: the pieces of the next DP_WIN_AHEAD steps, loaded that many steps
-    // ahead of their use
-    float4 pf[DP_WIN_AHEAD];
-#pragma unroll
-    for (int t = 0; t < DP_WIN_AHEAD; ++t)
-        pf[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // WIN: the lanes that copy each step's pieces, and the group's lane mask
     const bool win_loader = WIN && lam < 2 * (D / 4);
+    const unsigned grp_mask = G == 32 ? KNN_FULL_MASK : ((1u << G) - 1u) << gbase;
 
     float qw[U][D], xw[U][D];
     float E[P], O[P], mE[P], mO[P];
@@ -268,11 +287,17 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                             load_point_prefix<D>(xp, s0 + h + p, n - 1, xw[p]);
                         }
                         if constexpr (WIN) {
+                            // copies of the previous pair still in flight land
+                            // before any lane of the group refills the window
+                            cp_async_wait_all();
+                            __syncwarp(grp_mask);
                             // the (G-1)P rows and columns before the first step's
                             // newest, in float4 pieces spread over the group, copied
                             // global -> shared asynchronously (no registers, all
-                            // copies in flight at once); the step loop's __syncwarp
-                            // publishes them to the group after the wait below
+                            // copies in flight at once), then the pieces of the
+                            // first DP_WIN_AHEAD steps, one commit group each; the
+                            // step loop waits for them and its __syncwarp
+                            // publishes them to the group
                             const int h0 = lo / 2, hT = lo / 2 + P * (G - 1);
                             const int nf = (G - 1) * P * (D / 4);
                             for (int t = lam; t < nf; t += G) {
@@ -284,12 +309,14 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
                                 cp_async16(xwin + dp_win_slot<P>(cx, wp_mask) * RS + 4 * c,
                                            xp + (int64_t)clampi(cx, -1, n - 1) * D + 4 * c);
                             }
-                            if (win_loader) {
+                            cp_async_commit();
 #pragma unroll
-                                for (int t = 0; t < DP_WIN_AHEAD; ++t)
-                                    pf[t] = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s0 + t);
+                            for (int t = 0; t < DP_WIN_AHEAD; ++t) {
+                                if (win_loader)
+                                    dp_win_copy<D, P>(qwin, xwin, wp_mask, qp, xp, m, n, lam,
+                                                      h0, hT, s0 + t);
+                                cp_async_commit();
                             }
-                            cp_async_wait_all();
                         }
                         active = true;
                         st_calls += (lam == 0);
@@ -311,21 +338,16 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
         for (int u = 0; u < U; ++u) {
             const int s = s0 + u;
             if constexpr (WIN) {
-                // the group brings this step's newest row and column into its
-                // windows with coalesced loads; each lane then reads its own
-                // from shared memory instead of scattered global lines
+                // the group copies the newest row and column of step
+                // s + DP_WIN_AHEAD into its windows (coalesced, asynchronous)
+                // and waits for those of this step; each lane then reads its
+                // own from shared memory instead of scattered global lines
                 const int h0 = h - P * lam, hT = h0 + P * (G - 1);
-                if (win_loader) {
-                    const bool isx = lam >= D / 4;
-                    const int c = isx ? lam - D / 4 : lam;
-                    float *dst = isx ? xwin + dp_win_slot<P>(s + hT + P, wp_mask) * RS
-                                     : qwin + dp_win_slot<P>(s - h0, wp_mask) * RS;
-                    reinterpret_cast<float4 *>(dst)[c] = pf[0];
-#pragma unroll
-                    for (int t = 0; t + 1 < DP_WIN_AHEAD; ++t)
-                        pf[t] = pf[t + 1];
-                    pf[DP_WIN_AHEAD - 1] = dp_win_fetch<D>(qp, xp, m, n, lam, h0, hT, P, s + DP_WIN_AHEAD);
-                }
+                if (win_loader)
+                    dp_win_copy<D, P>(qwin, xwin, wp_mask, qp, xp, m, n, lam, h0, hT,
+                                      s + DP_WIN_AHEAD);
+                cp_async_commit();
+                cp_async_wait_group<DP_WIN_AHEAD>();
                 __syncwarp();
                 const float4 *qs =
                     reinterpret_cast<const float4 *>(qwin + dp_win_slot<P>(s - h, wp_mask) * RS);
@@ -428,6 +450,9 @@ __global__ void __launch_bounds__(DP_THREADS) dp_kernel(const DpArgs a)
             }
         }
     }
+
+    if constexpr (WIN)
+        cp_async_wait_all();  // no copy outlives the CTA
 
     // ---- counters: one atomic per warp per counter --------------------------
 #pragma unroll

@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(LBC_THREADS, 2) lb_coarse_kernel(const CoarseA
     const int tid = threadIdx.x, lane = tid & 31;
     __shared__ int mq[QT], qbs[QT];
     __shared__ float lim[QT];
+    __shared__ unsigned feas_one;  // bucket of one length: bit j = query j reaches it
     if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
         if (a.stats)
             atomicOr(a.stats + STAT_LB_KERNELS, 16ull);
@@ -218,6 +219,15 @@ __global__ void __launch_bounds__(LBC_THREADS, 2) lb_coarse_kernel(const CoarseA
             reinterpret_cast<const float4 *>(a.box_hi + (int64_t)qb * a.box_stride)[t];
     }
     __syncthreads();
+    // the band test |m - n| <= r(m, n) once per query when the bucket has a
+    // single length (published by the __syncthreads_or below)
+    static_assert(QT <= 32, "one warp holds the tile's queries");
+    if (tid < 32) {
+        const bool f = tid < nqt && abs(mq[tid] - a.n_lo) <= band_radius(mq[tid], a.n_lo, a.band);
+        const unsigned b = __ballot_sync(KNN_FULL_MASK, f);
+        if (tid == 0)
+            feas_one = b;
+    }
     const int nser = a.c_end - a.c_begin;
     unsigned long long st_pairs = 0, st_inf = 0, st_pruned = 0, st_cpr = 0, st_segs = 0;
     // a tile none of whose queries reaches a length of the bucket skips it
@@ -240,11 +250,20 @@ __global__ void __launch_bounds__(LBC_THREADS, 2) lb_coarse_kernel(const CoarseA
         const int nseg = n / a.W;
         const int nch = (nseg + PPC - 1) / PPC;
         const float4 *x4 = reinterpret_cast<const float4 *>(a.sg + a.sg_off[c]);
+        // bit j: query j's band reaches this series' end cell
+        unsigned fm = 0;
+        if (a.n_lo == a.n_hi) {
+            fm = valid ? feas_one : 0u;
+        } else {
+#pragma unroll
+            for (int j = 0; j < QT; ++j)
+                if (valid && j < nqt && abs(mq[j] - n) <= band_radius(mq[j], n, a.band))
+                    fm |= 1u << j;
+        }
         float acc[QT];
 #pragma unroll
         for (int j = 0; j < QT; ++j)
-            acc[j] = valid && j < nqt && abs(mq[j] - n) <= band_radius(mq[j], n, a.band)
-                         ? 0.f : KNN_INF;
+            acc[j] = (fm >> j) & 1u ? 0.f : KNN_INF;
         float4 nx[F4];
         if (nch > 0) {
 #pragma unroll
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(LBC_THREADS, 2) lb_coarse_kernel(const CoarseA
             if (j >= nqt)
                 break;
             const int qb = qbs[j];
-            const bool feasible = valid && abs(mq[j] - n) <= band_radius(mq[j], n, a.band);
+            const bool feasible = (fm >> j) & 1u;
             bool seeded = false;
             if (a.skip && feasible)
                 seeded = (a.skip[(int64_t)qb * a.skip_words + (c >> 5)] >> (c & 31)) & 1u;
