@@ -74,3 +74,41 @@ def test_query_shard_covers_the_batch_once():
     with pytest.raises(ValueError):
         query_shard(q_off, 0, 5, 3)
     assert max_over_ranks(3.5) == 3.5          # no process group: the value itself
+
+
+def _rank_fails(rank, world, port, out):
+    """Rank 1's step fails on the host (an exception before its collective);
+    rank 0 must learn of it from its next host collective, which ends with an
+    error within the process group's short timeout instead of waiting."""
+    import datetime
+    import time
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        # the failing step: no collective is in flight when the rank leaves
+        raise SystemExit(3)
+    t0 = time.time()
+    try:
+        max_over_ranks(1.0)
+        out.put(("no error", time.time() - t0))
+    except Exception as exc:  # the peer's exit surfaces here
+        out.put((type(exc).__name__, time.time() - t0))
+
+
+def test_a_failed_rank_is_reported_not_waited_for():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_fails, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    kind, waited = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[1].exitcode == 3
+    assert kind != "no error"
+    assert waited < 60
