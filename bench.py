@@ -78,13 +78,12 @@ PARITY_QUERIES, PARITY_OTHERS = 8, 192
 TOL = {0: 1e-5, 1: 1e-6}     # relative distance tolerance, DTW / DK
 
 
-# DRAM bytes (read + write) per launch of the dominant kernels on the bench
-# workloads, from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`
-# captures of the current kernels (the summaries in profiles/ give the commands).
+# DRAM bytes (read + write) of the dominant kernels on the bench workloads,
+# from one `ncu` capture of the current kernel on a reduced case of the same
+# workload, per unit of algorithmic work (a DP band cell): the roofline's
+# `traffic` is that figure times the units of the region `achieved` covers.
 # A kernel changed since its capture has no entry (traffic null).
-TRAFFIC = {
-    ("subseq_kernel", "subseq_d1_T1M_m256"): 5.78e6,
-}
+TRAFFIC_PER_UNIT = {}
 
 
 def peaks():
@@ -484,21 +483,27 @@ def run_gpu(args):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12
     stage = {"seed": 0.0, "lb": 0.0, "dp": 0.0, "finalize": 0.0}
-    dp_ops = lb_ops = 0.0
+    dp_ops = lb_ops = dp_units = 0.0
     for kind, s in prof.items():
         for k_ in stage:
             stage[k_] += s[f"ms_{k_}"]
         dp_ops += s["dp_cells"] * (2 * D + 3)
+        dp_units += s["dp_cells"]
         # exact LB_Box points and coarse segments cost the same per element
         lb_ops += (s["lb_points"] + s["lb_segments"]) * (4 * D + (1 if kind == kw.DK else 0))
     clocks = clk.summary()
     share = {k_: v / max(sum(stage.values()), 1e-12) for k_, v in stage.items()}
 
-    def alu_roof(kernel, ops, ms_):
+    def alu_roof(kernel, ops, ms_, units=0.0):
         achieved = ops / (ms_ / 1000.0) / 1e12 if ms_ else 0.0
+        per_unit = TRAFFIC_PER_UNIT.get((kernel, WORKLOAD))
+        traffic = None
+        if per_unit and units:
+            traffic = {"bytes": per_unit[0] * units, "bytes_per_unit": per_unit[0],
+                       "units": units, "source": per_unit[1]}
         r_ = {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": alu_peak,
               "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
-              "traffic": TRAFFIC.get((kernel, WORKLOAD)),
+              "traffic": traffic,
               "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz "
                              f"(max SM clock, {peak_src})",
               "timing": "CUDA events around the stage in one profiled scan per distance"}
@@ -515,7 +520,7 @@ def run_gpu(args):
                                          (8, "lb_compact_kernel"))
                        if lb_bits & b_) or "lb_multi_kernel"
     stage_roofs = {"lb": alu_roof(lb_name, lb_ops, stage["lb"]),
-                   "dp": alu_roof("dp_kernel", dp_ops, stage["dp"])}
+                   "dp": alu_roof("dp_kernel", dp_ops, stage["dp"], dp_units)}
     dominant = "lb" if stage["lb"] >= stage["dp"] else "dp"
     roof = dict(stage_roofs[dominant])
     roof["stage_share"] = share
@@ -944,7 +949,7 @@ def run_subseq(args):
     clocks = clk.summary()
     roof = {"kernel": "subseq_kernel", "bound": "alu", "achieved": achieved, "peak": alu_peak,
             "unit": "Tops/s (FP32 lane ops)", "frac": achieved / alu_peak,
-            "traffic": TRAFFIC.get(("subseq_kernel", args.workload)),
+            "traffic": None,
             "peak_source": f"{n_sm} SMs x 128 FP32 lanes x {sm_max_mhz:.0f} MHz (max SM clock, "
                            f"{peak_src})"}
     # end to end from host buffers (series and queries copied in every call)

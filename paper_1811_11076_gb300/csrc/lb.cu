@@ -218,7 +218,60 @@ __global__ void __launch_bounds__(LB_THREADS) lb_kernel(const LbArgs a)
             const int r = band_radius(m, n, a.band);
             const bool feasible = abs(m - n) <= r;
             float acc = 0.f;
-            if (feasible) {
+            if (feasible && D % 4 == 0) {
+                // points of whole float4 vectors (one point per chunk): the
+                // lanes take consecutive float4 of the series and of the
+                // envelope, so each warp load covers 512 contiguous bytes and
+                // each shared-memory read is free of bank conflicts; 16
+                // independent 16-byte loads in flight per lane.  The max form
+                // joins the FPP lanes of a point (xor shuffles) first.
+                constexpr int FPP = D / 4, NV = 16;
+                const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+                const int nf4 = n * FPP;
+                float acc4[4] = {0.f, 0.f, 0.f, 0.f};  // sum form: four FMA chains
+                for (int j0 = 0; j0 < nf4; j0 += 32 * NV) {
+                    float4 xv[NV];
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) {
+                        const int j = j0 + 32 * u + lane;
+                        xv[u] = __ldg(x4 + min(j, nf4 - 1));  // clamped; masked below
+                    }
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) {
+                        const int j = j0 + 32 * u + lane;
+                        // beyond the series: a zero element in a zero box
+                        const bool in = j < nf4;
+                        const float4 l4 = lo_s[min(j, nf4 - 1)], h4 = hi_s[min(j, nf4 - 1)];
+                        const float ex = in ? box_gap(xv[u].x, l4.x, h4.x) : 0.f;
+                        const float ey = in ? box_gap(xv[u].y, l4.y, h4.y) : 0.f;
+                        const float ez = in ? box_gap(xv[u].z, l4.z, h4.z) : 0.f;
+                        const float ew = in ? box_gap(xv[u].w, l4.w, h4.w) : 0.f;
+                        if constexpr (FORM == 0) {
+                            float &t = acc4[u & 3];
+                            t = __fmaf_rn(ex, ex, t);
+                            t = __fmaf_rn(ey, ey, t);
+                            t = __fmaf_rn(ez, ez, t);
+                            t = __fmaf_rn(ew, ew, t);
+                        } else {
+                            float t = __fmaf_rn(ex, ex, 0.f);
+                            t = __fmaf_rn(ey, ey, t);
+                            t = __fmaf_rn(ez, ez, t);
+                            t = __fmaf_rn(ew, ew, t);
+#pragma unroll
+                            for (int o = 1; o < FPP; o <<= 1)
+                                t += __shfl_xor_sync(KNN_FULL_MASK, t, o);
+                            acc = fmaxf(acc, t);
+                        }
+                    }
+                }
+                if constexpr (FORM == 0)
+                    acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float other = __shfl_xor_sync(KNN_FULL_MASK, acc, o);
+                    acc = FORM == 0 ? acc + other : fmaxf(acc, other);
+                }
+            } else if (feasible) {
                 const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
                 const int nch = (n + PPC - 1) / PPC;
                 // UNR chunks per lane per iteration: 16 independent 16-byte
