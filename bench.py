@@ -83,7 +83,14 @@ TOL = {0: 1e-5, 1: 1e-6}     # relative distance tolerance, DTW / DK
 # workload, per unit of algorithmic work (a DP band cell): the roofline's
 # `traffic` is that figure times the units of the region `achieved` covers.
 # A kernel changed since its capture has no entry (traffic null).
-TRAFFIC_PER_UNIT = {}
+TRAFFIC_PER_UNIT = {
+    # dp_kernel<16, 4, 0, WIN> on the first 50,000 series and 64 queries:
+    # 1,000.1 MB of DRAM traffic for 1,494.7 M band cells (each pair streams
+    # its series once, so the traffic follows the cells it sweeps)
+    ("dp_kernel", "highdim_d16_n500k_L512"): (
+        0.669, "ncu dram__bytes_read.sum + dram__bytes_write.sum of one DTW launch, "
+               "50,000 series x 64 queries, per band cell, scaled by the cells counted here"),
+}
 
 
 def peaks():

@@ -239,8 +239,9 @@ KNN_API int32_t knn_dp_shapes(int32_t d, int32_t *P_list, int32_t cap);
 
 /* Query tile of the LB_Box stream (Section 3, Eq. 1) for one distance: a
  * CTA bounds its 256 series against qtile queries at once (4, 8 or 16; 0 =
- * 16, or the tuned value) so that the database is read once per tile.
- * window_chunks = 0: a CTA stages the tile's whole envelopes in shared
+ * 16, or the tuned value) so that the database is read once per tile; the
+ * coarse first stage of the cascade takes the same tile (at most the number
+ * of segment boxes that fit in 100 KB of shared memory).  window_chunks = 0: a CTA stages the tile's whole envelopes in shared
  * memory when they fit (2 * 4 * qtile * padded length * d bytes <= 192 KB)
  * and windows of them otherwise; > 0: always windows of that many chunks of
  * lcm(d', 4) floats (clamped to what fits).  compaction (filter mode with

@@ -19,20 +19,29 @@ constexpr int FIN_THREADS = 128;
 
 // Banded DP in FP64 for one pair, computed by the threads of one CTA along
 // anti-diagonals t = i + j: every cell of an anti-diagonal is independent,
-// threads take the band diagonals delta = j - i of the right parity in
-// strides of 2 * blockDim.x, and the two previous anti-diagonals live in
-// shared memory (indexed by delta + r + 1, with an infinite sentinel on both
+// groups of four threads take the band diagonals delta = j - i of the right
+// parity in strides of 2 * blockDim.x / 4, and the two previous
+// anti-diagonals live in shared memory (indexed by delta + r + 1, with an infinite sentinel on both
 // sides).  Every in-band slot is rewritten on each anti-diagonal of its
 // parity (with +inf outside the matrix) and slots of the other parity are
 // never read, so the three rows rotate without clearing.  kind 0: DTW (sum
 // of squared costs); kind 1: DK^2 (max of squared costs).  Each cell applies
-// exactly the operations of the recurrence (products and sums rounded
-// separately, no fused multiply-add, coordinates in order), so the value
-// equals that of a sequential double-precision evaluation regardless of the
-// sweep order.  Shared memory: 3 * (2r + 3) doubles.  Called by all threads
-// of the CTA; returns the value in every thread.
+// the operations of the recurrence in a fixed order (the difference of two
+// FP32 coordinates is exact in double precision; each square is added with
+// one fused multiply-add to one of four partial sums, coordinates k mod 4,
+// which are then joined in a fixed order), so the value does not depend on
+// the sweep order and agrees with a sequential double-precision evaluation
+// to rounding (about 1e-15 relative per cell).  Shared memory: 3 * (2r + 3)
+// doubles.  Called by all threads of the CTA (a multiple of 4); returns the
+// value in every thread.
+//
+// stage != nullptr: the two series are first converted to double in shared
+// memory (rows of d + 1 doubles, so the rows that the threads of an
+// anti-diagonal read, one apart, fall in different banks), and every cell
+// then costs one subtraction and one fused multiply-add per coordinate
+// instead of two conversions more.  Same value either way.
 __device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int d, int r,
-                              int kind, double *buf)
+                              int kind, double *buf, double *stage = nullptr)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (abs(m - n) > r)
@@ -41,22 +50,52 @@ __device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int 
     double *A = buf, *B = buf + W, *Cc = buf + 2 * W;  // t-2, t-1, t
     for (int b = tid; b < 3 * W; b += nt)
         buf[b] = (double)KNN_INF;
+    const int ds = d + 1;
+    double *ss = stage, *st = stage ? stage + (int64_t)m * ds : nullptr;
+    if (stage) {
+        for (int i = tid; i < m; i += nt)
+            for (int k = 0; k < d; ++k)
+                ss[i * ds + k] = (double)s[(int64_t)i * d + k];
+        for (int j = tid; j < n; j += nt)
+            for (int k = 0; k < d; ++k)
+                st[j * ds + k] = (double)t[(int64_t)j * d + k];
+    }
     __syncthreads();
     const int tmax = m + n - 2;
+    // four threads per cell: thread q of a group sums the squares of the
+    // coordinates k = q (mod 4) (one FMA chain each), and the group joins the
+    // four partial sums as (c0 + c1) + (c2 + c3) through two shuffles
+    const int g = tid >> 2, ng = nt >> 2, q = tid & 3;
+    const unsigned gmask = 0xFu << ((tid & 31) & ~3);
     for (int tt = 0; tt <= tmax; ++tt) {
         // diagonals delta in [-r, r] with delta = tt (mod 2)
         const int d0 = -r + (((tt + r) & 1) ? 1 : 0);
-        for (int dl = d0 + 2 * tid; dl <= r; dl += 2 * nt) {
+        for (int dl = d0 + 2 * g; dl <= r; dl += 2 * ng) {
             const int i2 = tt - dl, j2 = tt + dl;  // 2i, 2j
             const int i = i2 >> 1, j = j2 >> 1;
-            double v = (double)KNN_INF;
-            if (i >= 0 && i < m && j >= 0 && j < n) {
-                double c = 0.0;
-                for (int k = 0; k < d; ++k) {
-                    const double df =
-                        __dsub_rn((double)s[(int64_t)i * d + k], (double)t[(int64_t)j * d + k]);
-                    c = __dadd_rn(c, __dmul_rn(df, df));
+            const bool in = i >= 0 && i < m && j >= 0 && j < n;
+            double c = 0.0;
+            if (in) {
+                if (stage) {
+                    const double *si = ss + i * ds, *tj = st + j * ds;
+                    for (int k = q; k < d; k += 4) {
+                        const double df = __dsub_rn(si[k], tj[k]);
+                        c = __fma_rn(df, df, c);
+                    }
+                } else {
+                    const float *sf = s + (int64_t)i * d, *tf = t + (int64_t)j * d;
+                    for (int k = q; k < d; k += 4) {
+                        const double df = __dsub_rn((double)sf[k], (double)tf[k]);
+                        c = __fma_rn(df, df, c);
+                    }
                 }
+            }
+            c = __dadd_rn(c, __shfl_xor_sync(gmask, c, 1));
+            c = __dadd_rn(c, __shfl_xor_sync(gmask, c, 2));
+            if (q != 0)
+                continue;
+            double v = (double)KNN_INF;
+            if (in) {
                 if (tt == 0) {
                     v = c;
                 } else {
@@ -79,12 +118,12 @@ __device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int 
 }
 
 // Threads of the re-scoring CTA for band rows of `row` slots: about one
-// diagonal of each parity per thread.
+// diagonal of each parity per group of four threads.
 static int fp64_threads(int row)
 {
     const int half = (row + 1) / 2;
-    int t = (half + 31) / 32 * 32;
-    return t < 32 ? 32 : (t > 256 ? 256 : t);
+    int t = (4 * half + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
 
 // ---------------------------------------------------------------------------
@@ -193,7 +232,7 @@ __global__ void __launch_bounds__(FIN_THREADS) fin_mark_kernel(const FinArgs a)
 // ---------------------------------------------------------------------------
 // 2. rescore: one CTA per picked entry
 
-__global__ void __launch_bounds__(256) fin_rescore_kernel(const FinArgs a)
+__global__ void __launch_bounds__(512) fin_rescore_kernel(const FinArgs a)
 {
     extern __shared__ double rbuf[];
     const int n_rer = min(*a.rer_count, a.rer_cap);
@@ -211,8 +250,11 @@ __global__ void __launch_bounds__(256) fin_rescore_kernel(const FinArgs a)
                 atomicOr(a.status, KNN_DEV_BAD_SHAPE);
             continue;
         }
+        // both series staged as doubles when they fit the launch's allotment
+        double *stage = (int64_t)(m + n) <= (int64_t)a.stage_pts ? rbuf + 3 * (a.rer_row + 2)
+                                                                 : nullptr;
         const double v = dp_fp64_cta(a.q + a.q_off[qb], m, a.db + a.db_off_by_id[id], n, a.d, r,
-                                     a.kind, rbuf);
+                                     a.kind, rbuf, stage);
         if (threadIdx.x == 0)
             a.fin_vals[(size_t)qb * a.fin_width + i] = v;
         __syncthreads();
@@ -540,7 +582,8 @@ void fin_init_attributes()
 
 int launch_finalize(const FinArgs &a, cudaStream_t st)
 {
-    const size_t smem_rer = (size_t)3 * (a.rer_row + 2) * sizeof(double);
+    const size_t smem_rer =
+        ((size_t)3 * (a.rer_row + 2) + (size_t)a.stage_pts * (a.d + 1)) * sizeof(double);
     const int rer_grid = a.rer_cap < 4096 ? a.rer_cap : 4096;
     if (a.k == 0 && a.eps_cap > FIN_SMALL_CAP) {
         int launches = 0;

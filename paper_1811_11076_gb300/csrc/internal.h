@@ -108,6 +108,7 @@ struct CoarseArgs {
     int64_t box_stride;
     int box_floats;
     int nseg_hi;                   // segments of the bucket's longest series
+    int qtile_req;                 // queries per CTA asked for (0: the most that fit)
     float M;                       // largest coordinate magnitude in the database
     const float *thr;
     float mu_prune;
@@ -121,11 +122,19 @@ struct CoarseArgs {
     unsigned long long *stats;
     int *status;
     uint32_t fault_wait_spins;     // tests only: see LbArgs
+    // per-query queue (nullable): pairs of batch query qb go to
+    // cq[qb * cq_stride ...], counted in cq_qcount[qb]; else one list
+    int *cq_qcount;
+    int64_t cq_stride;
 };
 struct PairLbArgs {
     const int2 *cq;                // (series, query) pairs
     const int *cq_count;
     int64_t cq_cap;
+    const int *cq_qcount;          // per-query queue (nullable), see CoarseArgs
+    int64_t cq_stride;
+    int nq;
+    int env_floats;                // floats of one envelope used by the bucket
     const float *db;
     const int64_t *db_off;
     const int *db_len;
@@ -148,6 +157,9 @@ void launch_seg_boxes(const SegBoxArgs &a, cudaStream_t st);
 // Queries per coarse CTA whose boxes fit in shared memory (0: none).
 int coarse_qtile(int box_floats);
 bool launch_lb_coarse(const CoarseArgs &a, int deff, int form, int n_sm, cudaStream_t st);
+// Whether the exact stage can take its pairs grouped by query, one query's
+// envelope in shared memory per CTA (d' a multiple of 4, envelope small enough).
+bool lb_pairs_by_query(int deff, int env_floats);
 bool launch_lb_pairs(const PairLbArgs &a, int deff, int form, int n_sm, cudaStream_t st);
 void lbc_init_attributes();
 
@@ -274,6 +286,8 @@ struct FinArgs {
     int *rer_count;
     int rer_cap;
     int rer_row;               // longest band row supported (2r+1)
+    int stage_pts;             // points of the two series of an entry staged as
+                               // doubles in shared memory (0: none)
     // data for FP64 re-scoring (caller ids -> database rows)
     const float *db;
     const int64_t *db_off_by_id;

@@ -331,14 +331,18 @@ __global__ void __launch_bounds__(LBC_THREADS, 2) lb_coarse_kernel(const CoarseA
             st_cpr += feasible && !seeded && !keep;
             const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
             if (kb) {
+                // one query per ballot: the warp's survivors go to its list
+                int *count = a.cq_qcount ? a.cq_qcount + qb : a.cq_count;
+                int2 *list = a.cq_qcount ? a.cq + (int64_t)qb * a.cq_stride : a.cq;
+                const int64_t cap = a.cq_qcount ? a.cq_stride : a.cq_cap;
                 int pos0 = 0;
                 if (lane == 0)
-                    pos0 = atomicAdd(a.cq_count, __popc(kb));
+                    pos0 = atomicAdd(count, __popc(kb));
                 pos0 = __shfl_sync(KNN_FULL_MASK, pos0, 0);
                 if (keep) {
                     const int64_t pos = (int64_t)pos0 + __popc(kb & ((1u << lane) - 1u));
-                    if (pos < a.cq_cap)
-                        a.cq[pos] = make_int2(c, qb);
+                    if (pos < cap)
+                        list[pos] = make_int2(c, qb);
                     else
                         atomicOr(a.status, KNN_DEV_CAPACITY);
                 }
@@ -559,6 +563,131 @@ __global__ void __launch_bounds__(LBP_THREADS) lb_pair4_kernel(const PairLbArgs 
     flush_stat(a.stats, STAT_LB_POINTS, st_points);
 }
 
+// The exact stage with its pairs grouped by query: CTA (slice, qb) copies
+// query qb's envelope (lower and upper, env_floats each) into shared memory
+// once and bounds its share of qb's survivors; lanes read the series as in
+// lb_pair4_kernel (consecutive float4, 128 B per group per load) and the
+// envelope from shared memory, where the four groups of a warp, in step on
+// the same query, read the same float4 (broadcast); eight float4 of the
+// series in flight per lane, the bound tested every two rounds (as often per
+// point as lb_pair4_kernel).  The series then come from DRAM alone instead of
+// series plus two envelope rows per point.
+template <int D, int FORM>
+__global__ void __launch_bounds__(LBP_THREADS, 3) lb_pairq4_kernel(const PairLbArgs a)
+{
+    static_assert(D % 4 == 0 && D <= 32, "whole float4 points");
+    constexpr int FPP = D / 4, UNR = 8, RF4 = LBP_GROUP * UNR, GPW = 32 / LBP_GROUP;
+    constexpr int GPB = (LBP_THREADS / 32) * GPW;  // pair groups per CTA
+    extern __shared__ __align__(16) float4 envq[];  // lo then hi, env_floats / 4 each
+    const int qb = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / LBP_GROUP, gl = lane % LBP_GROUP;
+    const int ef4 = a.env_floats / 4;
+    const float4 *lo_g = reinterpret_cast<const float4 *>(a.env_lo + (int64_t)qb * a.env_stride);
+    const float4 *hi_g = reinterpret_cast<const float4 *>(a.env_hi + (int64_t)qb * a.env_stride);
+    for (int i = threadIdx.x; i < ef4; i += blockDim.x) {
+        envq[i] = __ldg(lo_g + i);
+        envq[ef4 + i] = __ldg(hi_g + i);
+    }
+    __syncthreads();
+    const float4 *lo4 = envq, *hi4 = envq + ef4;
+    const int total = (int)min((int64_t)a.cq_qcount[qb], a.cq_stride);
+    const int2 *list = a.cq + (int64_t)qb * a.cq_stride;
+    const float lim = ld_volatile_f32(a.thr + qb) * a.mu_prune;
+    unsigned long long st_pruned = 0, st_points = 0;
+    const int stride = gridDim.x * GPB;
+    for (int base = blockIdx.x * GPB + warp * GPW; base < total; base += stride) {
+        const int idx = base + grp;
+        const bool valid = idx < total;
+        const int c = valid ? list[idx].x : 0;
+        const int n = valid ? a.db_len[c] : 0;
+        const float4 *x4 = reinterpret_cast<const float4 *>(a.db + a.db_off[c]);
+        const int nf4 = n * FPP;
+        const int nf4_max = __reduce_max_sync(KNN_FULL_MASK, nf4);
+        float acc[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            acc[u] = 0.f;
+        float tot = 0.f;
+        bool alive = valid;
+        for (int r0 = 0, round = 0; r0 < nf4_max; r0 += RF4, ++round) {
+            float4 xv[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int j = r0 + u * LBP_GROUP + gl;
+                if (alive && j < nf4) {
+                    xv[u] = __ldg(x4 + j);
+                    st_points += (j % FPP) == 0;
+                } else {
+                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int j = r0 + u * LBP_GROUP + gl;
+                // beyond the series (or the pair decided): a zero gap
+                const bool in = alive && j < nf4;
+                const int js = in ? j : 0;
+                const float4 l = lo4[js], h = hi4[js];
+                const float ex = in ? box_gap(xv[u].x, l.x, h.x) : 0.f;
+                const float ey = in ? box_gap(xv[u].y, l.y, h.y) : 0.f;
+                const float ez = in ? box_gap(xv[u].z, l.z, h.z) : 0.f;
+                const float ew = in ? box_gap(xv[u].w, l.w, h.w) : 0.f;
+                if constexpr (FORM == 0) {
+                    float t = acc[u];
+                    t = __fmaf_rn(ex, ex, t);
+                    t = __fmaf_rn(ey, ey, t);
+                    t = __fmaf_rn(ez, ez, t);
+                    acc[u] = __fmaf_rn(ew, ew, t);
+                } else {
+                    float t = __fmaf_rn(ex, ex, 0.f);
+                    t = __fmaf_rn(ey, ey, t);
+                    t = __fmaf_rn(ez, ez, t);
+                    t = __fmaf_rn(ew, ew, t);
+#pragma unroll
+                    for (int o = 1; o < FPP; o <<= 1)
+                        t += __shfl_xor_sync(KNN_FULL_MASK, t, o);
+                    acc[u] = fmaxf(acc[u], t);
+                }
+            }
+            if ((round & 1) == 1 || r0 + RF4 >= nf4_max) {
+                tot = acc[0];
+#pragma unroll
+                for (int u = 1; u < UNR; ++u)
+                    tot = FORM == 0 ? tot + acc[u] : fmaxf(tot, acc[u]);
+#pragma unroll
+                for (int o = 1; o < LBP_GROUP; o <<= 1) {
+                    const float other = __shfl_xor_sync(KNN_FULL_MASK, tot, o);
+                    tot = FORM == 0 ? tot + other : fmaxf(tot, other);
+                }
+                alive = alive && tot <= lim;
+                if (!__any_sync(KNN_FULL_MASK, alive))
+                    break;
+            }
+        }
+        const bool keep = alive && gl == 0;
+        st_pruned += valid && gl == 0 && !alive;
+        const unsigned kb = __ballot_sync(KNN_FULL_MASK, keep);
+        if (kb) {
+            int pos0 = 0;
+            if (lane == 0)
+                pos0 = atomicAdd(a.n_items, __popc(kb));
+            pos0 = __shfl_sync(KNN_FULL_MASK, pos0, 0);
+            if (keep) {
+                const int64_t pos = (int64_t)pos0 + __popc(kb & ((1u << lane) - 1u));
+                if (pos < a.capacity) {
+                    a.items[pos] = make_int2(c, qb);
+                    a.item_lb[pos] = tot;
+                } else {
+                    atomicOr(a.status, KNN_DEV_CAPACITY);
+                }
+            }
+        }
+    }
+    flush_stat(a.stats, STAT_LB_PRUNED, st_pruned);
+    flush_stat(a.stats, STAT_LB_POINTS, st_points);
+}
+
 }  // namespace
 
 void launch_seg_means(const float *data, const int64_t *off, const int *len, int N, int deff,
@@ -615,10 +744,33 @@ bool coarse_launch_d(const CoarseArgs &a, int form, int qt, int n_sm, cudaStream
                      : coarse_launch_q<D, 1>(a, qt, n_sm, st);
 }
 
+constexpr size_t LBPQ_SMEM_MAX = 200 * 1024;
+
 template <int D>
 void pair_launch_d(const PairLbArgs &a, int form, int n_sm, cudaStream_t st)
 {
     if constexpr (D % 4 == 0) {
+        if (a.cq_qcount) {
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(lb_pairq4_kernel<D, 0>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LBPQ_SMEM_MAX);
+                cudaFuncSetAttribute(lb_pairq4_kernel<D, 1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LBPQ_SMEM_MAX);
+                attr = true;
+            }
+            // slices per query: about six CTAs' worth per SM over the batch
+            const int slices = std::max(1, (6 * n_sm + a.nq - 1) / a.nq);
+            const size_t smem = (size_t)2 * a.env_floats * sizeof(float);
+            const dim3 grid(slices, a.nq);
+            if (form == 0)
+                lb_pairq4_kernel<D, 0><<<grid, LBP_THREADS, smem, st>>>(a);
+            else
+                lb_pairq4_kernel<D, 1><<<grid, LBP_THREADS, smem, st>>>(a);
+            return;
+        }
         if (form == 0)
             lb_pair4_kernel<D, 0><<<n_sm * 8, LBP_THREADS, 0, st>>>(a);
         else
@@ -660,7 +812,9 @@ int coarse_qtile(int box_floats)
 
 bool launch_lb_coarse(const CoarseArgs &a, int deff, int form, int n_sm, cudaStream_t st)
 {
-    const int qt = coarse_qtile(a.box_floats);
+    int qt = coarse_qtile(a.box_floats);
+    if (a.qtile_req > 0 && a.qtile_req < qt)
+        qt = a.qtile_req;
     switch (deff) {
     case 1: return coarse_launch_d<1>(a, form, qt, n_sm, st);
     case 2: return coarse_launch_d<2>(a, form, qt, n_sm, st);
@@ -673,6 +827,11 @@ bool launch_lb_coarse(const CoarseArgs &a, int deff, int form, int n_sm, cudaStr
     case 16: return coarse_launch_d<16>(a, form, qt, n_sm, st);
     default: return false;
     }
+}
+
+bool lb_pairs_by_query(int deff, int env_floats)
+{
+    return deff % 4 == 0 && (size_t)2 * env_floats * sizeof(float) <= LBPQ_SMEM_MAX;
 }
 
 bool launch_lb_pairs(const PairLbArgs &a, int deff, int form, int n_sm, cudaStream_t st)

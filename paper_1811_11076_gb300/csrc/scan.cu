@@ -225,7 +225,8 @@ knn_status size_workspace(knn_db *db, const Plan &pl)
         G_(sbox_lo, sizeof(float) * nq * pl.box_stride);
         G_(sbox_hi, sizeof(float) * nq * pl.box_stride);
         G_(cq, sizeof(int2) * pl.items_cap);
-        G_(cq_count, sizeof(int) * db->buckets.size());
+        // per bucket: the list's count, then one count per query
+        G_(cq_count, sizeof(int) * db->buckets.size() * (nq + 1));
     }
     G_(item_lb, sizeof(float) * pl.items_cap);
     G_(eps_list, sizeof(unsigned long long) * nq * std::max<int64_t>(pl.eps_cap, 1));
@@ -431,7 +432,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     // envelope + LB_Box stream per bucket (LB-ordered seeding: store every bound)
     const bool store = pl.seeded && !pl.learned;
     if (pl.box_stride > 0)
-        cudaMemsetAsync(ws.cq_count.p, 0, sizeof(int) * db->buckets.size(), st);
+        cudaMemsetAsync(ws.cq_count.p, 0, sizeof(int) * db->buckets.size() * (nq + 1), st);
     for (size_t bi = 0; bi < db->buckets.size(); ++bi) {
         const Bucket &b = db->buckets[bi];
         const Segment &sg = pl.segs[pl.seg_of_bucket[bi]];
@@ -470,7 +471,11 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
             sb.box_floats = box_floats;
             launch_seg_boxes(sb, st);
             int2 *cq = ws.cq.as<int2>() + (int64_t)nq * b.c_begin;
-            int *cq_count = ws.cq_count.as<int>() + bi;
+            int *cq_count = ws.cq_count.as<int>() + bi * (nq + 1);
+            const int env_floats = (int)((int64_t)((b.n_hi + PPC - 1) / PPC) * CH);
+            // pairs grouped by query when the exact stage can hold one
+            // query's envelope in shared memory
+            const bool by_query = lb_pairs_by_query(db->deff, env_floats);
             CoarseArgs c{};
             c.sg = db->sg.as<float>();
             c.sg_off = db->sg_off.as<int64_t>();
@@ -500,14 +505,23 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
             c.cq = cq;
             c.cq_count = cq_count;
             c.cq_cap = (int64_t)nq * (b.c_end - b.c_begin);
+            if (by_query) {
+                c.cq_qcount = cq_count + 1;
+                c.cq_stride = b.c_end - b.c_begin;
+            }
             c.stats = stats;
             c.status = &ctrl->status;
             c.fault_wait_spins = fault_wait_spins();
+            c.qtile_req = db->lb_qtile[kind];
             launch_lb_coarse(c, db->deff, kind, db->n_sm, st);
             PairLbArgs pr{};
             pr.cq = cq;
             pr.cq_count = cq_count;
             pr.cq_cap = c.cq_cap;
+            pr.cq_qcount = c.cq_qcount;
+            pr.cq_stride = c.cq_stride;
+            pr.nq = nq;
+            pr.env_floats = env_floats;
             pr.db = db->data.as<float>();
             pr.db_off = db->off.as<int64_t>();
             pr.db_len = db->len.as<int>();
@@ -660,6 +674,14 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
     f.rer_count = &ctrl->rer_count;
     f.rer_cap = pl.rer_cap;
     f.rer_row = pl.rer_row;
+    {
+        // stage an entry's query and series as doubles when both fit beside
+        // the band rows in 200 KB of shared memory
+        const int64_t pts = (int64_t)pl.max_m + db->max_len;
+        const size_t bytes =
+            ((size_t)3 * (pl.rer_row + 2) + (size_t)pts * (db->deff + 1)) * sizeof(double);
+        f.stage_pts = bytes <= 200 * 1024 ? (int)pts : 0;
+    }
     f.db = db->data.as<float>();
     f.db_off_by_id = db->off_by_id.as<int64_t>();
     f.db_len_by_id = db->len_by_id.as<int>();

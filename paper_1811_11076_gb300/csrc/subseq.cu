@@ -62,8 +62,9 @@ struct SubArgs {
 };
 
 // FP64 re-scoring: the candidate's value may be off by the FP32 rounding of
-// a path; it is recomputed exactly (subtractions, products and sums rounded
-// separately in coordinate order, no fused multiply-add) for every path whose
+// a path; it is recomputed in double precision (exact differences of the
+// FP32 coordinates, each square added by one fused multiply-add, coordinates
+// in order) for every path whose
 // value is at most T = v32 (1 + SUB_MARGIN).  A path from start column a to
 // end b crosses every column in between and so costs at least the sum (DTW)
 // or the max (DK) over those columns of the column's least cell cost; the
@@ -258,7 +259,7 @@ __device__ __forceinline__ double cost64(const float *x, const float *y)
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const double df = __dsub_rn((double)x[k], (double)y[k]);
-        c = __dadd_rn(c, __dmul_rn(df, df));
+        c = __fma_rn(df, df, c);
     }
     return c;
 }
