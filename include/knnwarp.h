@@ -257,7 +257,8 @@ KNN_API knn_status knn_get_lb_tile(knn_db *db, int32_t distance, int32_t *qtile,
 
 /* Coarse first stage of the LB_Box cascade (Section 3, Eq. 1 over segment
  * boxes).  The points of a series are grouped into segments of W consecutive
- * points (W = 16 for d >= 8, else 4; partial last segments left out), B_s is
+ * points (W = 4 for d < 8; for d >= 8, 64 when every series of the database
+ * has at least 256 points, else 16; partial last segments left out), B_s is
  * the smallest box holding the query envelope's boxes B_j of segment s, and
  *     LB_seg = sum_s W * dist(mean of the segment's points, B_s)^2
  * (form 0; form 1: the max over segments of dist^2) is at most LB_Box, by

@@ -358,7 +358,10 @@ static knn_status db_build(const float *series, const std::vector<int64_t> &hoff
 
     // coarse first stage of the LB_Box cascade: scaled segment means of every
     // series (full segments only) and the largest coordinate magnitude
-    const int W = coarse_width(deff);
+    int min_len = N > 0 ? db->h_len[0] : 0;
+    for (int c = 1; c < N; ++c)
+        min_len = std::min(min_len, db->h_len[c]);
+    const int W = coarse_width(deff, min_len);
     std::vector<int64_t> sg_off(N), sg_end(N);
     int64_t sg_total = 0;
     for (int c = 0; c < N; ++c) {

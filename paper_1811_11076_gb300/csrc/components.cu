@@ -185,7 +185,7 @@ static knn_status bound_common(knn_db *db, const float *query, int64_t m, float 
                 sb.d = db->deff;
                 sb.W = W;
                 sb.nseg = nseg;
-                sb.scale = W == 16 ? 4.f : 2.f;
+                sb.scale = coarse_scale(W);
                 sb.box_lo = ws.sbox_lo.as<float>();
                 sb.box_hi = ws.sbox_hi.as<float>();
                 sb.box_stride = box_floats;

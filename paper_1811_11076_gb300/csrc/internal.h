@@ -79,9 +79,19 @@ void launch_lb(const LbArgs &a, int d, int form, int n_sm, cudaStream_t st);
 void lb_init_attributes();
 
 // -- coarse first stage of the LB_Box cascade (segment boxes) ---------------
-// Segment width for a database of point width deff (a power of 4, so that
-// the sqrt(W) scaling of means and boxes is exact).
-inline int coarse_width(int deff) { return deff >= 8 ? 16 : 4; }
+// Segment width for a database of point width deff whose shortest series has
+// min_len points (a power of 4, so that the sqrt(W) scaling of means and
+// boxes is exact): wide points take 64-point segments when every series has
+// at least four of them (about as tight a filter as 16-point segments at a
+// quarter of the segment work and data), else 16; narrow points take 4.
+inline int coarse_width(int deff, int min_len)
+{
+    if (deff < 8)
+        return 4;
+    return min_len >= 4 * 64 ? 64 : 16;
+}
+// sqrt(W), exact for the widths above.
+inline float coarse_scale(int W) { return W == 64 ? 8.f : W == 16 ? 4.f : 2.f; }
 struct SegBoxArgs {
     const float *env_lo, *env_hi;  // [nq][env_stride] envelopes of one bucket
     int64_t env_stride;

@@ -694,7 +694,7 @@ void launch_seg_means(const float *data, const int64_t *off, const int *len, int
                       int W, const int64_t *sg_off, const int64_t *sg_end, float *sg,
                       cudaStream_t st)
 {
-    const float scale = W == 16 ? 4.f : 2.f;
+    const float scale = coarse_scale(W);
     const int blocks = (int)(((int64_t)N * 32 + 255) / 256);
     seg_means_kernel<<<blocks, 256, 0, st>>>(data, off, len, N, deff, W, scale, sg_off, sg_end,
                                              sg);

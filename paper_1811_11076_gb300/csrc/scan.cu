@@ -464,7 +464,7 @@ int enqueue_batch(knn_db *db, const Plan &pl, const knn_params &p, const float *
             sb.d = db->deff;
             sb.W = W;
             sb.nseg = nseg;
-            sb.scale = W == 16 ? 4.f : 2.f;
+            sb.scale = coarse_scale(W);
             sb.box_lo = ws.sbox_lo.as<float>();
             sb.box_hi = ws.sbox_hi.as<float>();
             sb.box_stride = pl.box_stride;

@@ -518,17 +518,18 @@ def test_autotune_and_cache(kw, tmp_path):
 # ---------------------------------------------------------------------------
 # coarse first stage of the LB_Box cascade (segment boxes)
 
-@pytest.mark.parametrize("d", [1, 2, 3, 5, 8, 12, 16])
+@pytest.mark.parametrize("d,L", [(1, 50), (2, 50), (3, 50), (5, 50), (8, 96), (12, 96),
+                                 (16, 96), (8, 256), (16, 300)])
 @pytest.mark.parametrize("form", [0, 1])
-def test_lb_seg_component(kw, d, form):
+def test_lb_seg_component(kw, d, L, form):
     """knn_lb_seg against the oracle's segment-box bound (same W, same band
-    radius), and never above knn_lb_box."""
+    radius), and never above knn_lb_box; W = 4 for d < 8, 16 or 64 (series
+    of at least 256 points) for d >= 8."""
     rng = np.random.default_rng(70 + d + 10 * form)
-    L = 96 if d >= 8 else 50
     w = make_workload(n_series=300, n_queries=2, d=d, length=L, n_classes=4, seed=60 + d)
     db = kw.KnnDB(cuda(w.db), w.db_off)
     _, W = db.get_lb_cascade(0)
-    assert W == (16 if d >= 8 else 4)
+    assert W == (4 if d < 8 else 64 if L >= 256 else 16)
     band = 0.1
     r = oracle.band_radius(L, L, f32(band))
     for qi in range(2):
@@ -542,12 +543,13 @@ def test_lb_seg_component(kw, d, form):
     db.close()
 
 
-@pytest.mark.parametrize("d,lengths", [(3, None), (3, (40, 200)), (8, (64, 160)), (16, None)])
-def test_coarse_stage_gives_identical_results(kw, d, lengths):
+@pytest.mark.parametrize("d,lengths,L", [(3, None, 80), (3, (40, 200), 80), (8, (64, 160), 80),
+                                         (16, None, 128), (16, None, 256)])
+def test_coarse_stage_gives_identical_results(kw, d, lengths, L):
     """Scans with the coarse first stage (default) and without it return the
     same rows bit for bit, for DTW and DK, k-NN under every seeding and
-    eps-NN; the stage runs and prunes."""
-    L = 128 if d == 16 else 80
+    eps-NN; the stage runs and prunes (16-point segments at d = 16, L = 128;
+    64-point ones at L = 256)."""
     w = make_workload(n_series=2500, n_queries=12, d=d, length=L, length_range=lengths,
                       n_classes=8, seed=90 + d)
     db = kw.KnnDB(cuda(w.db), w.db_off)
