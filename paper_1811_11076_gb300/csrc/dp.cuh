@@ -64,22 +64,22 @@ __device__ __forceinline__ void load_point_prefix(const float *p, int idx, int l
 
 // Squared distance of two wide points on packed FP32 pairs: two interleaved
 // partial sums (even and odd coordinates), each an FMA chain, joined at the
-// end.  `init` (0, or +inf for an out-of-band slot) starts the even chain:
-// 0 + x is exact and +inf absorbs everything, so this equals adding it at the
-// end, one instruction fewer.  Half the instructions of the scalar chain and
-// half its dependent length; the sum has at most D/2 + 2 roundings per term,
-// within the (d + 2) u bound.
+// end and added to `init` (0, or +inf for an out-of-band slot).  Half the
+// instructions of the scalar chain and half its dependent length; the sum has
+// at most D/2 + 2 roundings per term, within the (d + 2) u bound.  (Starting
+// the even chain at `init` instead saves an add but measured 2.5 % slower at
+// d = 16: the scheduler lost more than the instruction.)
 template <int D>
 __device__ __forceinline__ float sqdist_acc_p2(const float (&a)[D], const float (&b)[D], float init)
 {
     static_assert(D % 2 == 0, "pairs of coordinates");
-    float2 acc = make_float2(init, 0.f);
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < D; k += 2) {
         const float2 t = sub2(make_float2(a[k], a[k + 1]), make_float2(b[k], b[k + 1]));
         acc = __ffma2_rn(t, t, acc);
     }
-    return acc.x + acc.y;
+    return (acc.x + acc.y) + init;
 }
 
 // Point cost of the DP: packed pairs from d = 8 on.
