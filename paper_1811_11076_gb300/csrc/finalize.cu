@@ -16,23 +16,28 @@
 namespace knn {
 
 constexpr int FIN_THREADS = 128;
+// Threads that share one cell of the FP64 program (a power of two <= 32): four
+// give the SM seven warps per CTA at d = 16 (eight measured 35 % slower: three
+// shuffles per cell and half-empty FMA chains).
+constexpr int FP64_TPC = 4;
 
 // Banded DP in FP64 for one pair, computed by the threads of one CTA along
 // anti-diagonals t = i + j: every cell of an anti-diagonal is independent,
-// groups of four threads take the band diagonals delta = j - i of the right
-// parity in strides of 2 * blockDim.x / 4, and the two previous
-// anti-diagonals live in shared memory (indexed by delta + r + 1, with an infinite sentinel on both
-// sides).  Every in-band slot is rewritten on each anti-diagonal of its
-// parity (with +inf outside the matrix) and slots of the other parity are
-// never read, so the three rows rotate without clearing.  kind 0: DTW (sum
-// of squared costs); kind 1: DK^2 (max of squared costs).  Each cell applies
-// the operations of the recurrence in a fixed order (the difference of two
-// FP32 coordinates is exact in double precision; each square is added with
-// one fused multiply-add to one of four partial sums, coordinates k mod 4,
-// which are then joined in a fixed order), so the value does not depend on
-// the sweep order and agrees with a sequential double-precision evaluation
-// to rounding (about 1e-15 relative per cell).  Shared memory: 3 * (2r + 3)
-// doubles.  Called by all threads of the CTA (a multiple of 4); returns the
+// groups of FP64_TPC threads take the band diagonals delta = j - i of the
+// right parity in strides of 2 * blockDim.x / FP64_TPC, and the two previous
+// anti-diagonals live in shared memory (indexed by delta + r + 1, with an
+// infinite sentinel on both sides).  Every in-band slot is rewritten on each
+// anti-diagonal of its parity (with +inf outside the matrix) and slots of the
+// other parity are never read, so the three rows rotate without clearing.
+// kind 0: DTW (sum of squared costs); kind 1: DK^2 (max of squared costs).
+// Each cell applies the operations of the recurrence in a fixed order (the
+// difference of two FP32 coordinates is exact in double precision; thread q
+// of the cell's group adds the squares of the coordinates k = q mod FP64_TPC
+// with fused multiply-adds, and the group joins its partial sums pairwise by
+// xor shuffles, neighbours first), so the value does not depend on the sweep
+// order and agrees with a sequential double-precision evaluation to rounding
+// (about 1e-15 relative per cell).  Shared memory: 3 * (2r + 3) doubles.
+// Called by all threads of the CTA (a multiple of FP64_TPC); returns the
 // value in every thread.
 //
 // stage != nullptr: the two series are first converted to double in shared
@@ -62,11 +67,12 @@ __device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int 
     }
     __syncthreads();
     const int tmax = m + n - 2;
-    // four threads per cell: thread q of a group sums the squares of the
-    // coordinates k = q (mod 4) (one FMA chain each), and the group joins the
-    // four partial sums as (c0 + c1) + (c2 + c3) through two shuffles
-    const int g = tid >> 2, ng = nt >> 2, q = tid & 3;
-    const unsigned gmask = 0xFu << ((tid & 31) & ~3);
+    // FP64_TPC threads per cell: thread q of a group sums the squares of the
+    // coordinates k = q (mod FP64_TPC) (one FMA chain each), and the group
+    // joins the partial sums pairwise, ((c0 + c1) + (c2 + c3)) + ..., by shuffles
+    const int g = tid / FP64_TPC, ng = nt / FP64_TPC, q = tid % FP64_TPC;
+    const unsigned gmask = (FP64_TPC == 32 ? 0xFFFFFFFFu : ((1u << FP64_TPC) - 1u))
+                           << ((tid & 31) & ~(FP64_TPC - 1));
     for (int tt = 0; tt <= tmax; ++tt) {
         // diagonals delta in [-r, r] with delta = tt (mod 2)
         const int d0 = -r + (((tt + r) & 1) ? 1 : 0);
@@ -78,20 +84,21 @@ __device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int 
             if (in) {
                 if (stage) {
                     const double *si = ss + i * ds, *tj = st + j * ds;
-                    for (int k = q; k < d; k += 4) {
+                    for (int k = q; k < d; k += FP64_TPC) {
                         const double df = __dsub_rn(si[k], tj[k]);
                         c = __fma_rn(df, df, c);
                     }
                 } else {
                     const float *sf = s + (int64_t)i * d, *tf = t + (int64_t)j * d;
-                    for (int k = q; k < d; k += 4) {
+                    for (int k = q; k < d; k += FP64_TPC) {
                         const double df = __dsub_rn((double)sf[k], (double)tf[k]);
                         c = __fma_rn(df, df, c);
                     }
                 }
             }
-            c = __dadd_rn(c, __shfl_xor_sync(gmask, c, 1));
-            c = __dadd_rn(c, __shfl_xor_sync(gmask, c, 2));
+#pragma unroll
+            for (int o = 1; o < FP64_TPC; o <<= 1)
+                c = __dadd_rn(c, __shfl_xor_sync(gmask, c, o));
             if (q != 0)
                 continue;
             double v = (double)KNN_INF;
@@ -118,11 +125,11 @@ __device__ double dp_fp64_cta(const float *s, int m, const float *t, int n, int 
 }
 
 // Threads of the re-scoring CTA for band rows of `row` slots: about one
-// diagonal of each parity per group of four threads.
+// diagonal of each parity per group of FP64_TPC threads.
 static int fp64_threads(int row)
 {
     const int half = (row + 1) / 2;
-    int t = (4 * half + 31) / 32 * 32;
+    int t = (FP64_TPC * half + 31) / 32 * 32;
     return t < 32 ? 32 : (t > 512 ? 512 : t);
 }
 
