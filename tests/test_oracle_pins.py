@@ -258,6 +258,22 @@ def test_segment_box_bound(orc):
             assert orc.lb_seg(s, t, r, 1, form) == pytest.approx(box, rel=1e-12, abs=1e-12)
             for W in (2, 4, 16):
                 assert orc.lb_seg(s, t, r, W, form) <= box * (1 + 1e-12) + 1e-12
+    # the 64-point segments used for wide points on series of >= 256 points
+    positive = 0
+    for _ in range(6):
+        d = int(rng.integers(8, 17))
+        m = int(rng.integers(256, 320))
+        n = int(np.clip(m + rng.integers(-5, 6), 256, None))
+        r = int(rng.integers(abs(m - n), 30))
+        # smooth walks (on iid noise a 64-point mean sits inside its box)
+        s = np.cumsum(rand_series(rng, m, d), axis=0)
+        t = np.cumsum(rand_series(rng, n, d), axis=0) + 3.0
+        for form in (0, 1):
+            box = orc.lb_box(s, t, r, form=form)
+            seg = orc.lb_seg(s, t, r, 64, form)
+            assert seg <= box * (1 + 1e-12) + 1e-12
+            positive += seg > 0
+    assert positive > 0
     with open(os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")) as f:
         cases = json.load(f)["segment_box_cases"]
     for c in cases:
