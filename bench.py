@@ -845,11 +845,82 @@ def lb_stream(args) -> dict:
             "note": "call time includes the query upload, envelope and scatter kernels"}
 
 
+def cascade_study(args) -> dict:
+    """What a tighter second bound would prune, on the d = 16 workload's first
+    series (default 20,000) and 4 queries, DTW (Section 3 Eq. 1 and the
+    bounds that tighten it).  The threshold is each query's exact 50-th
+    distance (the scan's result); the candidates are the series whose LB_Box
+    (envelope on the query) is within it, i.e. the pairs the DP receives.
+    For them: the reverse bound LB_Box(Q, env(X)) (the GPU component with the
+    roles swapped: a one-series database holding the query) and the
+    LB_Improved-style bound (LB_Box plus the query against the envelope of the
+    series' projection onto the query's envelope, FP64 numpy).  Reports how
+    many DP pairs each would remove, and the coarse segment bound's pass rate
+    at the database's segment width."""
+    import torch
+    from scipy.ndimage import maximum_filter1d, minimum_filter1d
+    import paper_1811_11076_gb300 as kw
+    select_workload("highdim_d16_n500k_L512")
+    n_series = args.series or 20000
+    w = workload(1, n_series=n_series)
+    L = LENGTH
+    r = int(np.float64(np.float32(BAND)) * L)
+    db = kw.KnnDB(torch.from_numpy(w.db).cuda(), w.db_off)
+    _, W = db.get_lb_cascade(0)
+
+    def env(a):
+        return (minimum_filter1d(a, size=2 * r + 1, axis=0, mode="nearest"),
+                maximum_filter1d(a, size=2 * r + 1, axis=0, mode="nearest"))
+
+    def box_sum(x, lo, hi):
+        e = np.maximum(np.maximum(lo - x, x - hi), 0.0)
+        return float(np.sum(e * e))
+
+    rows = []
+    for qi in range(4):
+        q = w.query(qi)
+        qd = torch.from_numpy(q).cuda()
+        _, dist = db.scan(qd, np.array([0, L]), k=K, band=BAND, distance=kw.DTW,
+                          seed=kw.SEED_LB)
+        thr = float(dist[0, -1])
+        fwd = db.lb_box(qd, BAND, 0).cpu().numpy().astype(np.float64)
+        seg = db.lb_seg(qd, BAND, 0).cpu().numpy().astype(np.float64)
+        surv = np.nonzero(fwd <= thr)[0]
+        qdb = kw.KnnDB(qd, np.array([0, L]))
+        q64 = q.astype(np.float64)
+        qlo, qhi = env(q64)
+        rev = np.empty(surv.size)
+        imp = np.empty(surv.size)
+        for j, c in enumerate(surv):
+            x = w.series(int(c))
+            rev[j] = float(qdb.lb_box(torch.from_numpy(x).cuda(), BAND, 0)[0])
+            h = np.clip(x.astype(np.float64), qlo, qhi)
+            hlo, hhi = env(h)
+            imp[j] = fwd[c] + box_sum(q64, hlo, hhi)
+        qdb.close()
+        rows.append({"query": qi, "threshold": thr, "dp_pairs": int(surv.size),
+                     "removed_by_reverse": int(np.sum(rev > thr)),
+                     "removed_by_improved": int(np.sum(imp > thr)),
+                     "removed_by_either": int(np.sum((rev > thr) | (imp > thr))),
+                     "coarse_pass": float(np.mean(seg <= thr)),
+                     "lb_box_pass": float(np.mean(fwd <= thr))})
+    db.close()
+    tot = sum(x["dp_pairs"] for x in rows)
+    return {"workload": WORKLOAD, "n_series": n_series, "k": K, "band": BAND,
+            "segment_width": W, "queries": rows, "dp_pairs": tot,
+            "removed_by_either_frac": sum(x["removed_by_either"] for x in rows) / max(tot, 1)}
+
+
 def run_experiment(args):
     """Tightness sweep (the Theorem's trend) or 1-NN accuracy, one JSON line."""
     import paper_1811_11076_gb300 as kw
     kw.lib()
     t0 = time.perf_counter()
+    if args.experiment == "cascade":
+        line = {"experiment": "cascade", **cascade_study(args)}
+        line["seconds"] = time.perf_counter() - t0
+        print(json.dumps(line), flush=True)
+        return 0
     if args.experiment == "lbstream":
         line = {"experiment": "lbstream", **lb_stream(args)}
         line["seconds"] = time.perf_counter() - t0
@@ -1014,9 +1085,11 @@ def main():
     ap.add_argument("--only", default="both", choices=["both", "dtw", "dk"])
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--shape", default="", help="P,G: fix the DP shape instead of tuning it")
-    ap.add_argument("--experiment", default="", choices=["", "tightness", "accuracy", "lbstream"],
+    ap.add_argument("--experiment", default="",
+                    choices=["", "tightness", "accuracy", "lbstream", "cascade"],
                     help="instead of the throughput line: the LB_Box tightness sweep, the "
-                         "1-NN accuracy of DTW and DK, or the single-query LB_Box stream alone")
+                         "1-NN accuracy of DTW and DK, the single-query LB_Box stream alone, "
+                         "or what tighter second bounds would prune")
     ap.add_argument("--lb-qtile", type=int, default=0, choices=[0, 4, 8, 16],
                     help="queries per LB_Box pass (0: 16, or tuned)")
     ap.add_argument("--lb-compaction", type=int, default=0, choices=[0, 1, 2],
