@@ -634,7 +634,6 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_multi_kernel(const LbArgs a)
     lb_mark(a, 2ull);
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
-    constexpr int F4 = CH / 4;
     // [QT][env_floats] lo, then [QT][env_floats] hi: this bucket's envelopes
     extern __shared__ __align__(128) float4 env_s[];
     __shared__ __align__(8) uint64_t bar;
@@ -717,7 +716,6 @@ __global__ void __launch_bounds__(LB_THREADS, 2) lb_compact_kernel(const LbArgs 
     lb_mark(a, 8ull);
     constexpr int CH = chunk_floats(D);
     constexpr int PPC = chunk_points(D);
-    constexpr int F4 = CH / 4;
     extern __shared__ __align__(128) float4 env_s[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int qcnt[2], qhead[2], qpush[2];
